@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Benchmark of the sigma = H C build (determinants * sigma / s) on one GB300 per rank.
+
+Workload: plain FCI(14e, 14o), real FP64 integrals from the seeded generator
+(28 Cholesky vectors, seed 2), N = 3432 x 3432 = 11,778,624 determinants; a step is one
+sigma build (gather of D, the contraction E = g' D, the scatter into sigma) of a unit
+random vector (seed 7) resident in HBM.  Multi-GPU runs are independent replicas
+(the path does not shard on one-GPU machines): value = sum over ranks of N * K / T.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|oz_bf16|best]
+  python bench.py --impl reference    # the CPU oracle on a bounded sample of rows
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "determinants*sigma/s"
+WORKLOAD = "fci_14e14o"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="best", choices=["fp64", "oz_bf16", "best"])
+    ap.add_argument("--slices", type=int, default=7)
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-davidson", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- workload
+
+def make_inputs(name):
+    from paper_2505_20375_gb300 import synth
+
+    w = synth.WORKLOADS[name]
+    h, g = synth.real_integrals(w["n"], w["n_chol"], w["seed"])
+    return w, h, g
+
+
+def oracle_rate(w, h, g, c, seconds, rng_seed=11):
+    """The oracle as it stands, on a bounded sample of rows: rows/s (= det*sigma/s)."""
+    import oracle
+
+    hso, gso = oracle.spin_orbital_integrals(h, g)
+    dets = oracle.fci_dets(w["n"], w["na"], w["nb"])
+    N = len(dets)
+    perm = np.random.default_rng(rng_seed).permutation(N)
+    done, t_used, chunk = 0, 0.0, 2000
+    while t_used < seconds and done < N:
+        rows = perm[done:done + chunk]
+        t0 = time.perf_counter()
+        oracle.sigma(hso, gso, dets, c, rows=rows)
+        t_used += time.perf_counter() - t0
+        done += len(rows)
+        chunk = min(chunk * 2, 200000)
+    return done / t_used, done, t_used, oracle.num_threads()
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.out.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(a, rank, world, local_rank):
+    import torch
+
+    from paper_2505_20375_gb300 import fci, synth
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w, h, g = make_inputs(a.workload)
+    t0 = time.perf_counter()
+    f = fci.FCI(local_rank).setup_integrals(h, g).build_strings(w["na"], w["nb"])
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    N = f.n_det
+    c_np = synth.random_vector(N, seed=7)
+    C = torch.from_numpy(c_np).to(dev)
+    out = torch.empty_like(C)
+    stream = torch.cuda.current_stream()
+
+    # choose the precision: the fastest path that meets the FP64 parity bar
+    prec = a.precision
+    slices = a.slices
+    variants = {}
+
+    def sigma(p, s):
+        return f.sigma(C, precision=p, n_slices=s, out=out)
+
+    ref = sigma("fp64", 0).clone()
+    torch.cuda.synchronize()
+    try:
+        oz = sigma("oz_bf16", slices).clone()
+        oz_ok = True
+        err = (oz - ref).abs().max().item() / ref.abs().max().item()
+        variants[f"oz_bf16_s{slices}"] = {"rel_err_vs_fp64": err}
+    except fci.FCIError as e:
+        oz_ok = False
+        variants["oz_bf16"] = {"unavailable": str(e)[:200]}
+    if prec == "best":
+        prec = "oz_bf16" if (oz_ok and variants[f"oz_bf16_s{slices}"]["rel_err_vs_fp64"] <= 1e-11) else "fp64"
+    n_sl = slices if prec == "oz_bf16" else 0
+
+    # FP64 peak of this GPU, measured in this run (cuBLAS DGEMM through torch)
+    fp64_peak = None
+    try:
+        x = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        torch.matmul(x, x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = 1e30
+        for _ in range(3):
+            e0.record()
+            torch.matmul(x, x)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        fp64_peak = 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+        del x
+    except Exception:
+        pass
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    for _ in range(a.warmup):
+        sigma(prec, n_sl)
+    torch.cuda.synchronize()
+
+    f.set_phase_timing(True)
+    f.phase_times(reset=True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for i in range(a.steps):
+        flush.fill_(float(i))  # untimed: evicts C and sigma from L2 between steps
+        evs[i][0].record(stream)
+        sigma(prec, n_sl)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    phases = f.phase_times(reset=True)
+    f.set_phase_timing(False)
+    T = sum(step_ms) / 1e3
+
+    # end to end through the public call with HOST buffers (copies inside the timed region)
+    C_host = torch.from_numpy(c_np).pin_memory()
+    S_host = torch.empty_like(C_host).pin_memory()
+    f.sigma(C_host, precision=prec, n_slices=n_sl, out=S_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(a.steps):
+        f.sigma(C_host, precision=prec, n_slices=n_sl, out=S_host)
+    torch.cuda.synchronize()
+    T_e2e = time.perf_counter() - t0
+
+    # time-to-energy (FP64 Davidson vs mixed split-precision Davidson)
+    davidson = None
+    if not a.no_davidson and rank == 0:
+        davidson = {}
+        for name, kw in (("fp64", dict(precision="fp64")),
+                         ("mixed_oz_bf16_s3", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4))):
+            try:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = f.davidson(tol_residual=1e-5, tol_energy=1e-9, **kw)
+                torch.cuda.synchronize()
+                davidson[name] = {"seconds": time.perf_counter() - t0, "energy": r.energy,
+                                  "iterations": len(r.iterations), "sigma_builds": r.n_sigma,
+                                  "converged": r.converged,
+                                  "final_residual": r.iterations[-1]["residual_norm"] if r.iterations else None}
+            except fci.FCIError as e:
+                davidson[name] = {"unavailable": str(e)[:200]}
+        if "energy" in davidson.get("fp64", {}) and "energy" in davidson.get("mixed_oz_bf16_s3", {}):
+            davidson["mixed_oz_bf16_s3"]["energy_error_vs_fp64"] = abs(
+                davidson["mixed_oz_bf16_s3"]["energy"] - davidson["fp64"]["energy"])
+
+    # max over ranks
+    if world > 1:
+        t = torch.tensor([T, T_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        T, T_e2e = t.tolist()
+
+    value = world * N * a.steps / T
+    e2e = world * N * a.steps / T_e2e
+    # roofline of the dominant kernel (the contraction)
+    ph = phases["contract"]
+    npair = f.info["n_pair"]
+    flops_launch = 2.0 * npair * npair * N
+    ms_launch = ph["ms"] / max(ph["launches"], 1)
+    if prec == "fp64":
+        achieved = flops_launch / (ms_launch * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_dgemm (FP64 FMA)", "achieved": achieved,
+                "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp64_peak) if fp64_peak else None, "traffic": None,
+                "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 is not in MEASURED_PEAKS.json)"}
+    else:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
+        pad_m, pad_k = 128, 112
+        bf16_flops = 2.0 * pad_m * pad_k * N * (n_sl * (n_sl + 1) // 2)
+        achieved = bf16_flops / (ms_launch * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "kernel": "k_oz_contract (tcgen05 bf16)", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        rate, rows, secs, thr = oracle_rate(w, h, g, c_np, a.cpu_seconds)
+        cpu = {"value": rate, "unit": METRIC, "cores": thr, "kind": "oracle",
+               "sample": f"{rows} sigma rows of {a.workload} (Slater-Condon, one row per determinant) in {secs:.1f} s"}
+
+    launches = sum(p["launches"] for p in phases.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1e3 * T / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if prec == "fp64" else f"f64 (bf16 x{n_sl} split, int64 accumulate)",
+        "data": "synthetic (seeded integrals and vector)",
+        "config": {"workload": f"{a.workload}: FCI(14e,14o), N={N}, 28 Cholesky vectors, seed 2",
+                   "precision": prec, "n_slices": n_sl, "parallelism": f"replicas x{world}",
+                   "l2": "256 MB buffer written between timed steps (untimed)",
+                   "setup_s": setup_s},
+        "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "phases_ms_per_step": {k: v["ms"] / a.steps for k, v in phases.items()},
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "variants": variants,
+        "davidson": davidson,
+        "fp64_peak_tflops_measured": fp64_peak,
+    }
+    return line
+
+
+# ------------------------------------------------------------ reference arm
+
+def run_reference(a):
+    from paper_2505_20375_gb300 import synth
+
+    w, h, g = make_inputs(a.workload)
+    N = synth.WORKLOADS[a.workload]
+    from math import comb
+
+    N = comb(w["n"], w["na"]) * comb(w["n"], w["nb"])
+    c = synth.random_vector(N, seed=7)
+    per_step = max(a.cpu_seconds / max(a.steps, 1), 1.0)
+    for _ in range(a.warmup):
+        oracle_rate(w, h, g, c, 0.5)
+    tot_rows, tot_t, thr = 0, 0.0, 1
+    for k in range(a.steps):
+        rate, rows, secs, thr = oracle_rate(w, h, g, c, per_step, rng_seed=100 + k)
+        tot_rows += rows
+        tot_t += secs
+    value = tot_rows / tot_t
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * tot_t / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded integrals and vector)",
+            "config": {"workload": f"{a.workload}: FCI(14e,14o), N={N}", "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": thr, "kind": "oracle",
+                             "sample": f"{tot_rows} sigma rows over {a.steps} steps"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(a)))
+        return
+    if world > 1:
+        import torch
+
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(a, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

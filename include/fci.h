@@ -1,0 +1,249 @@
+/*
+ * fci.h -- C ABI of libfci: the sigma = H C build of string-based configuration
+ * interaction (CI) inside a Davidson eigensolver, on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (arXiv 2505.20375, "Methods", Eqs. sigmaL, sigmaL1e, sigmaL2e):
+ *   H = e_core + sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs) (E_pq E_rs - delta_qr E_ps)
+ *     = e_core + sum_pq h'_pq E_pq + 1/2 sum_pqrs (pq|rs) E_pq E_rs,
+ *   h'_pq = h_pq - 1/2 sum_r (pr|rq),
+ * over determinants built from occupation strings: alpha x beta strings of n spatial
+ * orbitals (real, spin-free integrals) or single strings of n spinors (complex
+ * Hermitian integrals, the paper's two-spinor X2C case).  sigma is evaluated as
+ *   D[rs,K] = sum_J <K|E_rs|J> C_J           (gather over single replacements)
+ *   E[pq,K] = sum_rs g'_pqrs D[rs,K]          (dense contraction, on tensor cores)
+ *   sigma_I = 1/2 sum_pq sum_K <I|E_pq|K> E[pq,K]   (gather-back over replacements)
+ * with g'_pqrs = (pq|rs) + (h'_pq delta_rs + delta_pq h'_rs)/N_e folding the one-electron
+ * term into the contraction (sum_r E_rr = N_e on an N_e-electron space).
+ *
+ * Conventions (all tables compare bit for bit with an independent CPU code):
+ *   - a string is a bit mask, orbital p = bit p; strings are listed in ascending integer
+ *     order, so the index of a string is its combinadic rank sum_j C(p_j, j) over its
+ *     occupied orbitals p_1 < p_2 < ... (0-based p, 1-based j);
+ *   - determinant |I> = prod_{p in alpha, ascending} a+_{p,alpha} prod_{p in beta,
+ *     ascending} a+_{p,beta} |0>; address I = I_alpha * N_beta + I_beta;
+ *   - the single-replacement list of string S holds, for each occupied a (ascending)
+ *     and each b (ascending) empty in S or equal to a, the string T = S - a + b, the
+ *     pair (a, b) and the sign <S|a+_a a_b|T> = (-1)^(number of electrons of S strictly
+ *     between a and b).  It has n_e (n_h + 1) entries per string, the size the paper's
+ *     Introduction gives for one-electron excitation lists.
+ *
+ * Memory: every large buffer (CI vectors, sigma, workspaces, Davidson subspace) is
+ * allocated by the caller on the handle's device and passed as a plain device pointer;
+ * the library borrows it for the duration of the call.  The handle owns only small
+ * device arrays (integrals, string tables, category metadata).  Calls that take a
+ * stream are asynchronous on it unless stated otherwise.
+ *
+ * Errors: every function returns an fci_status; on failure fci_last_error(h) returns
+ * a message (valid until the next call on h).  Invalid arguments never reach a kernel.
+ */
+#ifndef FCI_H
+#define FCI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fci_context *fci_handle;
+/* A cudaStream_t passed as an opaque pointer (NULL = the legacy default stream). */
+typedef void *fci_stream;
+
+typedef enum {
+    FCI_OK = 0,
+    FCI_ERR_ARG = 1,            /* invalid argument or size */
+    FCI_ERR_OOM = 2,            /* a device or host allocation failed (nothing leaked) */
+    FCI_ERR_CUDA = 3,           /* a CUDA runtime error; message in fci_last_error */
+    FCI_ERR_NOT_CONVERGED = 4,  /* Davidson hit max_iter; best Ritz pair returned */
+    FCI_ERR_TIMEOUT = 5,        /* a bounded device-side wait expired */
+    FCI_ERR_UNSUPPORTED = 6,    /* valid request this build does not implement */
+    FCI_ERR_STATE = 7           /* call out of order (e.g. sigma before strings) */
+} fci_status;
+
+enum { FCI_R64 = 0, FCI_C128 = 1 };              /* integral / vector element type */
+enum { FCI_MODE_NONE = 0, FCI_MODE_FCI = 1, FCI_MODE_SPINOR = 2, FCI_MODE_DAS = 3 };
+enum {
+    FCI_PREC_FP64 = 0,      /* every step in IEEE binary64 */
+    FCI_PREC_OZ_BF16 = 1    /* contraction split into bf16 slices on tcgen05 (Ozaki) */
+};
+
+typedef struct {
+    int mode;               /* FCI_MODE_* */
+    int dtype;              /* FCI_R64 or FCI_C128 */
+    int n_orb;              /* spatial orbitals (FCI, DAS) or spinors (SPINOR) */
+    int n_alpha, n_beta;    /* electrons per spin; SPINOR: n_alpha = electrons, n_beta = -1 */
+    int n_pair;             /* rows of D/E: n(n+1)/2 (real, pair-packed) or n*n (complex) */
+    int n_ent_alpha, n_ent_beta;   /* single-replacement entries per string */
+    int64_t n_str_alpha, n_str_beta;
+    int64_t n_det;          /* length of C and sigma */
+    int64_t n_det_intermediate;    /* DAS: determinants of the intermediate space */
+    int n_categories;       /* DAS target categories (0 otherwise) */
+    int n_categories_intermediate;
+} fci_info;
+
+/* ---------------------------------------------------------------- handles */
+
+/* Create a handle bound to CUDA device `device` (made current for every later call on
+ * the handle).  *out receives the handle, or NULL on failure. */
+int fci_create(fci_handle *out, int device);
+/* Free the handle's own device arrays.  Safe on NULL. */
+int fci_destroy(fci_handle h);
+/* Message of the last failed call on h ("" if none).  h may be NULL (global message). */
+const char *fci_last_error(fci_handle h);
+/* Fill *out with the handle's current problem description. */
+int fci_get_info(fci_handle h, fci_info *out);
+
+/* Number of determinants C(n,k) products for a space, on the host (no device use):
+ * FCI: C(n,na) C(n,nb); SPINOR (nb < 0): C(n,na).  Returns -1 on overflow/bad input. */
+int64_t fci_count_determinants(int n_orb, int n_alpha, int n_beta);
+
+/* ------------------------------------------------------------- problem setup */
+
+/* Integrals of the Hamiltonian above (Methods, Eq. sigmaL1e uses h', Eq. sigmaL2e g).
+ *   n_orb: 1..32 (R64) or 1..64 (C128);
+ *   h1: HOST pointer, n_orb x n_orb row-major, double (R64) or interleaved complex
+ *       (C128, h_pq = conj(h_qp));
+ *   g2: HOST pointer, (pq|rs) at ((p*n+q)*n+r)*n+s, chemists' notation, same type;
+ *       R64 needs the 8-fold symmetry of real orbitals, C128 needs (pq|rs) = (rs|pq)
+ *       and conj((pq|rs)) = (qp|sr).  Symmetry is checked to 1e-12 (FCI_ERR_ARG).
+ *   e_core: constant added to H.
+ * Copies both arrays; may be called again to replace the integrals of a handle. */
+int fci_setup_integrals(fci_handle h, int n_orb, int dtype, const void *h1, const void *g2,
+                        double e_core, fci_stream stream);
+
+/* Build the occupation strings and their single-replacement lists on the device
+ * (string enumeration by combinadic unranking; list targets ranked with warp ballots
+ * and popc).  n_beta >= 0: alpha/beta strings, FCI determinants (needs R64 integrals);
+ * n_beta < 0: one spinor string of n_alpha electrons per determinant (needs C128).
+ * Must follow fci_setup_integrals.  Resets any DAS layout.  Synchronous. */
+int fci_build_strings(fci_handle h, int n_alpha, int n_beta, fci_stream stream);
+
+/* STP-DAS layout (Results: categorical decomposition C = (+)_B C^B; Methods: the
+ * categorical sigma build).  The n_orb orbitals are split into n_spaces contiguous
+ * ranges of orbs_per_space[s] orbitals.  Per spin, a pattern is the tuple of electron
+ * counts per space; a category is an (alpha pattern, beta pattern) pair whose
+ * spin-resolved excess over the reference occupation (ref_alpha, ref_beta per space),
+ * summed over spaces and spins, is at most max_transfer.  Categories are ordered
+ * lexicographically, blocks are row-major [alpha-local][beta-local], local indices are
+ * mixed-radix over spaces (space 0 most significant) of per-space string ranks.
+ * Afterwards C and sigma are in DAS order (info.n_det entries), and sigma is P H P
+ * over the DAS space: the intermediate determinants of the resolution E_pq E_rs range
+ * over the categories within max_transfer + 1.  Requires R64 alpha/beta strings of
+ * n_orb <= 32.  Synchronous. */
+int das_build_categories(fci_handle h, int n_spaces, const int *orbs_per_space,
+                         const int *ref_alpha, const int *ref_beta, int max_transfer,
+                         fci_stream stream);
+
+/* H_II for every determinant of the current layout into the device array diag
+ * (info.n_det doubles; real also for C128, where H_II is real). */
+int fci_diagonal(fci_handle h, double *diag, fci_stream stream);
+
+/* ------------------------------------------------------------------- sigma */
+
+/* Bytes of device workspace fci_sigma needs for n_vec vectors at this precision. */
+int fci_sigma_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slices,
+                              size_t *bytes);
+
+/* sigma = H C for n_vec vectors (Methods, Eqs. sigmaL, sigmaL1e, sigmaL2e).
+ *   C, sigma: DEVICE pointers, n_vec x info.n_det, vector-major, double (R64) or
+ *             interleaved complex (C128); must not overlap;
+ *   precision: FCI_PREC_FP64, or FCI_PREC_OZ_BF16 with n_slices in [2, 8] bf16 slices
+ *             of each operand of the contraction (R64 only);
+ *   workspace: DEVICE pointer, >= fci_sigma_workspace_bytes, 256-byte aligned.
+ * Asynchronous on `stream`. */
+int fci_sigma(fci_handle h, const void *C, void *sigma, int n_vec, int precision,
+              int n_slices, void *workspace, size_t workspace_bytes, fci_stream stream);
+
+/* ---------------------------------------------------------------- Davidson */
+
+typedef struct {
+    int max_iter;           /* default 100 */
+    int max_subspace;       /* 2..32, default 32; collapse to the last two Ritz vectors */
+    double tol_residual;    /* ||r|| threshold, default 1e-6 */
+    double tol_energy;      /* |dE| threshold, default 1e-10 */
+    double eps;             /* compression-compatible preconditioner threshold (Eq.
+                               sparsePreconditioner), default 0 = Davidson's own */
+    int precision;          /* FCI_PREC_* used for sigma in the first phase */
+    int n_slices;           /* slices for FCI_PREC_OZ_BF16 */
+    double switch_residual; /* mixed mode: once ||r|| <= this, restart from the Ritz
+                               vector with FP64 sigma (default 1e-5) */
+    int use_guess;          /* 1: start from C_io; 0: unit vector at min H_II */
+} fci_davidson_opts;
+
+typedef struct {
+    int iteration;
+    int precision;          /* precision of the sigma used in this iteration */
+    double energy;          /* Ritz value + e_core */
+    double delta_energy;    /* energy - previous energy (0 on the first iteration) */
+    double max_delta_c;     /* max_i |c_i - c_i(previous)| (0 on the first) */
+    double residual_norm;   /* ||sigma_c - E c|| */
+    double seconds;         /* wall time of the iteration */
+} fci_davidson_iter;
+
+typedef struct {
+    int n_iter;             /* iterations recorded in iters (<= capacity) */
+    int converged;
+    int n_sigma;            /* sigma builds performed */
+    int capacity;           /* caller sets: length of iters (may be 0 with iters NULL) */
+    fci_davidson_iter *iters;
+} fci_davidson_log;
+
+/* Default options. */
+void fci_davidson_default_opts(fci_davidson_opts *opts);
+
+/* Device workspace davidson_solve needs (subspace vectors, sigma vectors, diagonal,
+ * scratch and the fci_sigma workspace). */
+int fci_davidson_workspace_bytes(fci_handle h, const fci_davidson_opts *opts, size_t *bytes);
+
+/* Lowest eigenpair by Davidson (Results: Ritz residual appended each iteration,
+ * preconditioner of Eq. sparsePreconditioner with guard |lambda - H_ii| >= 1e-12).
+ * All vector work, the projected eigenproblem and the Rayleigh quotient run on the
+ * device in FP64; the host only reads the Ritz value and residual norm per iteration.
+ *   C_io: DEVICE pointer, info.n_det elements: guess in (if opts->use_guess), Ritz
+ *         vector out (unit norm);
+ *   energy: HOST pointer, receives the lowest Ritz value + e_core;
+ *   log: optional HOST pointer (per-iteration table of the paper's Tables 1-3).
+ * Synchronous.  Returns FCI_ERR_NOT_CONVERGED (with the best pair) at max_iter. */
+int davidson_solve(fci_handle h, const fci_davidson_opts *opts, void *C_io, double *energy,
+                   fci_davidson_log *log, void *workspace, size_t workspace_bytes,
+                   fci_stream stream);
+
+/* ------------------------------------------------------------ table export */
+
+enum {
+    FCI_TABLE_STRINGS_ALPHA = 0,    /* uint64[n_str_alpha] masks (SPINOR: the strings) */
+    FCI_TABLE_STRINGS_BETA = 1,     /* uint64[n_str_beta] */
+    FCI_TABLE_REPL_ALPHA = 2,       /* int32[n_str_alpha * n_ent_alpha * 4]: per entry
+                                       {target, a, b, sign} */
+    FCI_TABLE_REPL_BETA = 3,
+    FCI_TABLE_DAS_CATEGORIES = 4,   /* int64[n_cat * (2*n_spaces + 3)]: alpha pattern,
+                                       beta pattern, n_alpha_str, n_beta_str, offset */
+    FCI_TABLE_DAS_ADDRESS = 5       /* int64[n_det]: FCI address of each DAS determinant */
+};
+
+/* Bytes of a table (0 if the table does not exist in the current layout). */
+int fci_table_bytes(fci_handle h, int table, size_t *bytes);
+/* Copy a table into a caller DEVICE buffer of at least fci_table_bytes bytes. */
+int fci_copy_table(fci_handle h, int table, void *dst, size_t bytes, fci_stream stream);
+
+
+/* ------------------------------------------------------------ phase timing */
+
+enum { FCI_PHASE_GATHER = 0, FCI_PHASE_CONTRACT = 1, FCI_PHASE_SCATTER = 2, FCI_PHASE_OTHER = 3,
+       FCI_N_PHASES = 4 };
+
+/* Enable (1) or disable (0) CUDA-event timing of the sigma phases (gather of D, the
+ * contraction E = g' D, the scatter into sigma, other kernels).  Events are recorded on
+ * the stream each kernel is launched on.  Adds no synchronisation to fci_sigma. */
+int fci_set_phase_timing(fci_handle h, int enable);
+/* Synchronise with the recorded events and return, per phase, the summed kernel time
+ * in milliseconds (ms[FCI_N_PHASES]) and the number of kernel launches
+ * (launches[FCI_N_PHASES]); either pointer may be NULL.  reset != 0 clears the sums. */
+int fci_get_phase_times(fci_handle h, double *ms, int64_t *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FCI_H */

@@ -1,0 +1,599 @@
+// Davidson eigensolver on the device (Results: the Ritz residual r = H C - E C is
+// preconditioned and appended as the next expansion vector; Eq. sparsePreconditioner).
+//
+// Every vector operation runs here in FP64 (complex vectors as interleaved pairs):
+// subspace projections V^H w, Ritz combinations, the residual, the preconditioner with
+// its 1e-12 guard and eps * ||s|| threshold, two rounds of classical Gram-Schmidt and
+// the projected eigenproblem (cyclic Jacobi in one thread block; complex Hermitian
+// matrices through their real symmetric embedding [[A, -B], [B, A]]).  The host reads
+// back a handful of scalars per iteration to decide convergence.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "fci_internal.h"
+
+namespace {
+
+constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
+constexpr int RED_THREADS = 256;
+constexpr int KMAX = 32;
+
+struct dav_scalars {      // device-resident scalars, read back each iteration
+    double lam;           // lowest Ritz value (without e_core)
+    double rnorm2, snorm2, maxdc;
+    double ov_re, ov_im;  // <c_prev|c>
+    double tnorm2;
+    double pad;
+};
+
+// partial[b][i] (complex: 2 doubles) = sum over this block's slice of conj(V_i) x
+template <bool CPLX>
+__global__ void __launch_bounds__(RED_THREADS) k_multidot(const double *__restrict__ V, int64_t ldv, int k,
+                                                          const double *__restrict__ x, int64_t n,
+                                                          double *__restrict__ partial) {
+    __shared__ double red[RED_THREADS / 32][2 * KMAX];
+    double acc_re[KMAX], acc_im[KMAX];
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) { acc_re[i] = 0.0; acc_im[i] = 0.0; }
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (CPLX) {
+            const double xr = x[2 * j], xi = x[2 * j + 1];
+#pragma unroll
+            for (int i = 0; i < KMAX; ++i) {
+                if (i < k) {
+                    const double vr = V[i * 2 * ldv + 2 * j], vi = V[i * 2 * ldv + 2 * j + 1];
+                    acc_re[i] = fma(vr, xr, fma(vi, xi, acc_re[i]));
+                    acc_im[i] = fma(vr, xi, fma(-vi, xr, acc_im[i]));
+                }
+            }
+        } else {
+            const double xr = x[j];
+#pragma unroll
+            for (int i = 0; i < KMAX; ++i)
+                if (i < k) acc_re[i] = fma(V[i * ldv + j], xr, acc_re[i]);
+        }
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+        if (i >= k) break;
+        double a = acc_re[i], b = acc_im[i];
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+            b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        }
+        if (lane == 0) { red[wid][2 * i] = a; red[wid][2 * i + 1] = b; }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * k) {
+        double s = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) s += red[w][threadIdx.x];
+        partial[(int64_t)blockIdx.x * 2 * KMAX + threadIdx.x] = s;
+    }
+}
+
+// out[i] (complex) = sum_b partial[b][i]; fixed order, so the result is reproducible.
+__global__ void k_reduce_partial(const double *__restrict__ partial, int nb, int k, double *__restrict__ out) {
+    const int i = threadIdx.x;
+    if (i >= 2 * k) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * 2 * KMAX + i];
+    out[i] = s;
+}
+
+// out = sum_i y_i V_i  (+ beta * out when accumulate), y complex as 2 doubles per entry.
+template <bool CPLX>
+__global__ void k_lincomb(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ y,
+                          double scale, int64_t n, double *__restrict__ out, int accumulate) {
+    __shared__ double sy[2 * KMAX];
+    if (threadIdx.x < 2 * k) sy[threadIdx.x] = y[threadIdx.x] * scale;
+    __syncthreads();
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (CPLX) {
+            double re = accumulate ? out[2 * j] : 0.0, im = accumulate ? out[2 * j + 1] : 0.0;
+            for (int i = 0; i < k; ++i) {
+                const double vr = V[i * 2 * ldv + 2 * j], vi = V[i * 2 * ldv + 2 * j + 1];
+                re = fma(sy[2 * i], vr, fma(-sy[2 * i + 1], vi, re));
+                im = fma(sy[2 * i], vi, fma(sy[2 * i + 1], vr, im));
+            }
+            out[2 * j] = re;
+            out[2 * j + 1] = im;
+        } else {
+            double acc = accumulate ? out[j] : 0.0;
+            for (int i = 0; i < k; ++i) acc = fma(sy[2 * i], V[i * ldv + j], acc);
+            out[j] = acc;
+        }
+    }
+}
+
+// Phase-align (c, sc) to c_prev by the scalar ph = conj(ov)/|ov|, then
+//   r = sc - lam c;  s_i = r_i / (lam - H_ii) if |lam - H_ii| >= 1e-12 else 0;  t = s.
+// Partial sums: ||r||^2, ||s||^2; partial max |c - c_prev|.
+template <bool CPLX>
+__global__ void __launch_bounds__(RED_THREADS) k_residual(double *__restrict__ c, double *__restrict__ sc,
+                                                          const double *__restrict__ cprev, int have_prev,
+                                                          const double *__restrict__ diag,
+                                                          const dav_scalars *__restrict__ sc_in, int64_t n,
+                                                          double *__restrict__ t, double *__restrict__ partial) {
+    const double lam = sc_in->lam;
+    double pr = 1.0, pi = 0.0;
+    if (have_prev) {
+        const double ore = sc_in->ov_re, oim = sc_in->ov_im, m = sqrt(ore * ore + oim * oim);
+        if (m > 0) { pr = ore / m; pi = -oim / m; }
+    }
+    double r2 = 0.0, s2 = 0.0, mdc = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double den = lam - diag[j];
+        const bool ok = fabs(den) >= 1e-12;
+        if (CPLX) {
+            double cr = c[2 * j], ci = c[2 * j + 1], sr = sc[2 * j], si = sc[2 * j + 1];
+            double a = cr * pr - ci * pi, b = cr * pi + ci * pr;
+            cr = a; ci = b;
+            a = sr * pr - si * pi; b = sr * pi + si * pr;
+            sr = a; si = b;
+            c[2 * j] = cr; c[2 * j + 1] = ci; sc[2 * j] = sr; sc[2 * j + 1] = si;
+            const double rr = sr - lam * cr, ri = si - lam * ci;
+            r2 += rr * rr + ri * ri;
+            const double tr = ok ? rr / den : 0.0, ti = ok ? ri / den : 0.0;
+            s2 += tr * tr + ti * ti;
+            t[2 * j] = tr; t[2 * j + 1] = ti;
+            if (have_prev) {
+                const double dr = cr - cprev[2 * j], di = ci - cprev[2 * j + 1];
+                mdc = fmax(mdc, sqrt(dr * dr + di * di));
+            }
+        } else {
+            double cr = c[j] * pr, sr = sc[j] * pr;
+            c[j] = cr; sc[j] = sr;
+            const double rr = sr - lam * cr;
+            r2 += rr * rr;
+            const double tr = ok ? rr / den : 0.0;
+            s2 += tr * tr;
+            t[j] = tr;
+            if (have_prev) mdc = fmax(mdc, fabs(cr - cprev[j]));
+        }
+    }
+    __shared__ double red[3][RED_THREADS / 32];
+    for (int o = 16; o; o >>= 1) {
+        r2 += __shfl_xor_sync(0xFFFFFFFFu, r2, o);
+        s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
+        mdc = fmax(mdc, __shfl_xor_sync(0xFFFFFFFFu, mdc, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { red[0][wid] = r2; red[1][wid] = s2; red[2][wid] = mdc; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, m = 0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) { a += red[0][w]; b += red[1][w]; m = fmax(m, red[2][w]); }
+        partial[blockIdx.x * 4 + 0] = a;
+        partial[blockIdx.x * 4 + 1] = b;
+        partial[blockIdx.x * 4 + 2] = m;
+    }
+}
+
+__global__ void k_reduce_residual(const double *__restrict__ partial, int nb, dav_scalars *__restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double a = 0, b = 0, m = 0;
+    for (int i = 0; i < nb; ++i) { a += partial[i * 4]; b += partial[i * 4 + 1]; m = fmax(m, partial[i * 4 + 2]); }
+    out->rnorm2 = a;
+    out->snorm2 = b;
+    out->maxdc = m;
+}
+
+// Compression-compatible threshold: t_i = 0 where |t_i| < eps ||s||.
+template <bool CPLX>
+__global__ void k_threshold(double *__restrict__ t, int64_t n, const dav_scalars *__restrict__ s, double eps) {
+    const double thr = eps * sqrt(s->snorm2);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (CPLX) {
+            const double a = t[2 * j], b = t[2 * j + 1];
+            if (sqrt(a * a + b * b) < thr) { t[2 * j] = 0.0; t[2 * j + 1] = 0.0; }
+        } else if (fabs(t[j]) < thr) {
+            t[j] = 0.0;
+        }
+    }
+}
+
+// Squared norm partials of x (complex counted as 2n reals).
+__global__ void __launch_bounds__(RED_THREADS) k_norm2(const double *__restrict__ x, int64_t nreal,
+                                                       double *__restrict__ partial) {
+    double a = 0.0;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nreal; j += (int64_t)gridDim.x * blockDim.x)
+        a = fma(x[j], x[j], a);
+    __shared__ double red[RED_THREADS / 32];
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) s += red[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_reduce_norm(const double *__restrict__ partial, int nb, double *__restrict__ out) {
+    if (threadIdx.x != 0) return;
+    double s = 0;
+    for (int i = 0; i < nb; ++i) s += partial[i];
+    *out = s;
+}
+
+// x *= 1/sqrt(*n2) (or *scale directly when n2 == nullptr)
+__global__ void k_scale(double *__restrict__ x, int64_t nreal, const double *__restrict__ n2) {
+    const double f = 1.0 / sqrt(*n2);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nreal; j += (int64_t)gridDim.x * blockDim.x)
+        x[j] *= f;
+}
+
+// Negate a complex coefficient vector (k entries).
+__global__ void k_negate(double *__restrict__ y, int k) {
+    if (threadIdx.x < 2 * k) y[threadIdx.x] = -y[threadIdx.x];
+}
+
+// Hsub column/row update: Hsub[i][k] = dots[i] for i <= k, Hsub[k][i] = conj(dots[i]).
+__global__ void k_hsub_update(double *__restrict__ Hs, const double *__restrict__ dots, int k) {
+    const int i = threadIdx.x;
+    if (i > k) return;
+    Hs[2 * (i * KMAX + k)] = dots[2 * i];
+    Hs[2 * (i * KMAX + k) + 1] = dots[2 * i + 1];
+    Hs[2 * (k * KMAX + i)] = dots[2 * i];
+    Hs[2 * (k * KMAX + i) + 1] = -dots[2 * i + 1];
+    if (i == k) Hs[2 * (k * KMAX + k) + 1] = 0.0;
+}
+
+// Lowest eigenpair of the k x k Hermitian Hs (leading dimension KMAX, complex entries)
+// by cyclic Jacobi on the real symmetric embedding of size m = k (real) or 2k (complex).
+// Writes y (complex, k entries) and lam.  One block of 64 threads.
+__global__ void __launch_bounds__(64) k_jacobi(const double *__restrict__ Hs, int k, int cplx,
+                                               double *__restrict__ y, dav_scalars *__restrict__ out) {
+    extern __shared__ double jac_smem[];  // A and Q, each m x (m + 1)
+    __shared__ double cs[2];
+    __shared__ int stop;
+    const int m = cplx ? 2 * k : k;
+    const int ld = m + 1;
+    double *Ab = jac_smem, *Qb = jac_smem + m * ld;
+#define A(r, c) Ab[(r) * ld + (c)]
+#define Q(r, c) Qb[(r) * ld + (c)]
+    const int t = threadIdx.x;
+    for (int i = t; i < m * m; i += blockDim.x) {
+        const int r = i / m, c = i % m;
+        double v;
+        if (!cplx) {
+            v = Hs[2 * (r * KMAX + c)];
+        } else {
+            const int rb = r / k, cb = c / k, rr = r % k, cc = c % k;
+            const double re = Hs[2 * (rr * KMAX + cc)], im = Hs[2 * (rr * KMAX + cc) + 1];
+            v = (rb == cb) ? re : (rb == 1 ? im : -im);
+        }
+        A(r, c) = v;
+        Q(r, c) = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        if (t == 0) {
+            double off = 0.0, tot = 0.0;
+            for (int r = 0; r < m; ++r)
+                for (int c = 0; c < m; ++c) {
+                    tot += A(r, c) * A(r, c);
+                    if (r != c) off += A(r, c) * A(r, c);
+                }
+            stop = (off <= 1e-30 * tot) || off == 0.0;
+        }
+        __syncthreads();
+        if (stop) break;
+        for (int p = 0; p < m - 1; ++p) {
+            for (int q = p + 1; q < m; ++q) {
+                if (t == 0) {
+                    const double apq = A(p, q);
+                    double c = 1.0, s = 0.0;
+                    if (fabs(apq) > 1e-300) {
+                        const double theta = (A(q, q) - A(p, p)) / (2.0 * apq);
+                        const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        s = tt * c;
+                    }
+                    cs[0] = c;
+                    cs[1] = s;
+                }
+                __syncthreads();
+                const double c = cs[0], s = cs[1];
+                if (s != 0.0) {
+                    if (t < m) {  // columns p, q of A and Q
+                        const double ap = A(t, p), aq = A(t, q);
+                        A(t, p) = c * ap - s * aq;
+                        A(t, q) = s * ap + c * aq;
+                        const double qp = Q(t, p), qq = Q(t, q);
+                        Q(t, p) = c * qp - s * qq;
+                        Q(t, q) = s * qp + c * qq;
+                    }
+                    __syncthreads();
+                    if (t < m) {  // rows p, q of A
+                        const double ap = A(p, t), aq = A(q, t);
+                        A(p, t) = c * ap - s * aq;
+                        A(q, t) = s * ap + c * aq;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    if (t == 0) {
+        int best = 0;
+        for (int i = 1; i < m; ++i)
+            if (A(i, i) < A(best, best)) best = i;
+        out->lam = A(best, best);
+        double nrm = 0.0;
+        for (int i = 0; i < k; ++i) {
+            const double re = Q(i, best), im = cplx ? Q(k + i, best) : 0.0;
+            y[2 * i] = re;
+            y[2 * i + 1] = im;
+            nrm += re * re + im * im;
+        }
+        nrm = 1.0 / sqrt(nrm);
+        for (int i = 0; i < 2 * k; ++i) y[i] *= nrm;
+    }
+}
+#undef A
+#undef Q
+
+// argmin of diag (lowest index on ties) -> unit vector
+__global__ void k_argmin(const double *__restrict__ d, int64_t n, int64_t *__restrict__ out) {
+    __shared__ double bv[256];
+    __shared__ int64_t bi[256];
+    double v = INFINITY;
+    int64_t idx = 0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+        if (d[j] < v) { v = d[j]; idx = j; }
+    bv[threadIdx.x] = v;
+    bi[threadIdx.x] = idx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double best = INFINITY;
+        int64_t b = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i)
+            if (bv[i] < best || (bv[i] == best && bi[i] < b)) { best = bv[i]; b = bi[i]; }
+        *out = b;
+    }
+}
+
+__global__ void k_set_unit(double *__restrict__ x, int64_t nreal, int cplx, const int64_t *__restrict__ idx) {
+    const int64_t at = (cplx ? 2 : 1) * (*idx);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nreal; j += (int64_t)gridDim.x * blockDim.x)
+        x[j] = (j == at) ? 1.0 : 0.0;
+}
+
+inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct dav_ws {
+    double *V, *S, *c, *sc, *cp, *scp, *t, *diag;
+    void *sig_ws;
+    size_t sig_bytes;
+};
+
+}  // namespace
+
+size_t davidson_ws_bytes(const fci_context *h, const fci_davidson_opts *o) {
+    const int64_t n = h->das_active ? h->das.n_det : h->ndet;
+    const size_t esz = h->dtype == FCI_C128 ? 16 : 8;
+    const size_t vec = al((size_t)n * esz);
+    size_t sig = sigma_ws_bytes(h, o->precision, o->n_slices);
+    if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, FCI_PREC_FP64, 0));
+    return 2 * (size_t)o->max_subspace * vec + 5 * vec + al((size_t)n * 8) + al(sig);
+}
+
+int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, double *energy, fci_davidson_log *log,
+                 void *ws, size_t ws_bytes, cudaStream_t s) {
+    (void)ws_bytes;
+    const int64_t n = h->das_active ? h->das.n_det : h->ndet;
+    const bool cplx = h->dtype == FCI_C128;
+    const size_t esz = cplx ? 16 : 8;
+    const int64_t nreal = cplx ? 2 * n : n;
+    const size_t vec = al((size_t)n * esz);
+    const int ms = o->max_subspace;
+    char *p = (char *)ws;
+    dav_ws w;
+    w.V = (double *)p; p += ms * vec;
+    w.S = (double *)p; p += ms * vec;
+    w.c = (double *)p; p += vec;
+    w.sc = (double *)p; p += vec;
+    w.cp = (double *)p; p += vec;
+    w.scp = (double *)p; p += vec;
+    w.t = (double *)p; p += vec;
+    w.diag = (double *)p; p += al((size_t)n * 8);
+    w.sig_ws = p;
+    size_t sig = sigma_ws_bytes(h, o->precision, o->n_slices);
+    if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, FCI_PREC_FP64, 0));
+    w.sig_bytes = al(sig);
+    const int64_t ldv = (int64_t)(vec / esz);  // elements between consecutive subspace vectors
+
+    // small device scratch inside the handle's buffer
+    double *small = h->d_small;
+    double *partial = small;                                  // RED_BLOCKS * 2 * KMAX
+    double *Hs = partial + RED_BLOCKS * 2 * KMAX;             // 2 * KMAX * KMAX
+    double *dots = Hs + 2 * KMAX * KMAX;                      // 2 * KMAX
+    double *y = dots + 2 * KMAX;                              // 2 * KMAX
+    double *nrm = y + 2 * KMAX;                               // 4
+    dav_scalars *scal = (dav_scalars *)(nrm + 4);
+    int64_t *argmin = (int64_t *)(scal + 1);
+
+    const unsigned vb = (unsigned)std::min<int64_t>(RED_BLOCKS, std::max<int64_t>(1, ceil_div(n, RED_THREADS)));
+
+    auto multidot = [&](const double *Vb, int k, const double *x, double *out) -> cudaError_t {
+        if (cplx) k_multidot<true><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, x, n, partial);
+        else k_multidot<false><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, x, n, partial);
+        k_reduce_partial<<<1, 64, 0, s>>>(partial, vb, k, out);
+        return cudaGetLastError();
+    };
+    auto lincomb = [&](const double *Vb, int k, const double *yy, double scale, double *out, int acc) -> cudaError_t {
+        if (cplx) k_lincomb<true><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, yy, scale, n, out, acc);
+        else k_lincomb<false><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, yy, scale, n, out, acc);
+        return cudaGetLastError();
+    };
+    auto normalize = [&](double *x, double *n2out) -> cudaError_t {
+        k_norm2<<<vb, RED_THREADS, 0, s>>>(x, nreal, partial);
+        k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, n2out);
+        k_scale<<<vb, RED_THREADS, 0, s>>>(x, nreal, n2out);
+        return cudaGetLastError();
+    };
+    auto Vk = [&](int i) { return (double *)((char *)w.V + (size_t)i * vec); };
+    auto Sk = [&](int i) { return (double *)((char *)w.S + (size_t)i * vec); };
+    int n_sigma = 0;
+    int prec = o->precision;
+    auto sigma = [&](const double *x, double *out) -> int {
+        ++n_sigma;
+        return sigma_dispatch(h, x, out, prec, o->n_slices, w.sig_ws, w.sig_bytes, s);
+    };
+    // New subspace column k: Hs[:, k] = V^H S_k.
+    auto add_column = [&](int k) -> int {
+        FCI_CUDA(h, multidot(w.V, k + 1, Sk(k), dots));
+        k_hsub_update<<<1, 64, 0, s>>>(Hs, dots, k);
+        FCI_CUDA(h, cudaGetLastError());
+        return FCI_OK;
+    };
+
+    int rc;
+    FCI_CUDA(h, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     2 * (2 * KMAX) * (2 * KMAX + 1) * (int)sizeof(double)));
+    // diagonal and start vector
+    if (h->das_active) FCI_CUDA(h, launch_diag_das(h, w.diag, s));
+    else if (h->mode == FCI_MODE_SPINOR) FCI_CUDA(h, launch_diag_spinor(h, w.diag, s));
+    else FCI_CUDA(h, launch_diag_fci(h, w.diag, s));
+    if (o->use_guess) {
+        FCI_CUDA(h, cudaMemcpyAsync(Vk(0), C_io, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_argmin<<<1, 256, 0, s>>>(w.diag, n, argmin);
+        k_set_unit<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, cplx, argmin);
+    }
+    FCI_CUDA(h, normalize(Vk(0), nrm));
+    if ((rc = sigma(Vk(0), Sk(0)))) return rc;
+    FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
+    if ((rc = add_column(0))) return rc;
+    int k = 1;
+    bool have_prev = false;
+    bool converged = false;
+    double E_prev = 0.0;
+    int it_rec = 0;
+    int phase1_iters = 0;
+    dav_scalars hs{};
+    for (int it = 1; it <= o->max_iter; ++it) {
+        auto t0 = std::chrono::steady_clock::now();
+        {
+            const int m = cplx ? 2 * k : k;
+            k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, y, scal);
+        }
+        FCI_CUDA(h, lincomb(w.V, k, y, 1.0, w.c, 0));
+        FCI_CUDA(h, lincomb(w.S, k, y, 1.0, w.sc, 0));
+        if (have_prev) {
+            FCI_CUDA(h, multidot(w.cp, 1, w.c, dots));  // <c_prev|c>
+            FCI_CUDA(h, cudaMemcpyAsync(&scal->ov_re, dots, 16, cudaMemcpyDeviceToDevice, s));
+        }
+        if (cplx) k_residual<true><<<vb, RED_THREADS, 0, s>>>(w.c, w.sc, w.cp, have_prev, w.diag, scal, n, w.t, partial);
+        else k_residual<false><<<vb, RED_THREADS, 0, s>>>(w.c, w.sc, w.cp, have_prev, w.diag, scal, n, w.t, partial);
+        k_reduce_residual<<<1, 32, 0, s>>>(partial, vb, scal);
+        FCI_CUDA(h, cudaGetLastError());
+        FCI_CUDA(h, cudaMemcpyAsync(&hs, scal, sizeof hs, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(h, cudaStreamSynchronize(s));
+        const double lam = hs.lam, rn = sqrt(hs.rnorm2);
+        const double dE = it > 1 ? lam - E_prev : 0.0;
+        auto t1 = std::chrono::steady_clock::now();
+        if (log && log->iters && it_rec < log->capacity) {
+            fci_davidson_iter &r = log->iters[it_rec];
+            r.iteration = it;
+            r.precision = prec;
+            r.energy = lam + h->e_core;
+            r.delta_energy = dE;
+            r.max_delta_c = have_prev ? hs.maxdc : 0.0;
+            r.residual_norm = rn;
+            r.seconds = std::chrono::duration<double>(t1 - t0).count();
+        }
+        ++it_rec;
+        if (!isfinite(lam) || !isfinite(rn)) return fci_fail(h, FCI_ERR_CUDA, "Davidson produced a non-finite value");
+        if (prec != FCI_PREC_FP64) {
+            ++phase1_iters;
+            if (rn <= o->switch_residual || phase1_iters >= o->max_iter / 2) {
+                // Residual correction: restart from the Ritz vector with FP64 sigma.
+                prec = FCI_PREC_FP64;
+                FCI_CUDA(h, cudaMemcpyAsync(Vk(0), w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                FCI_CUDA(h, normalize(Vk(0), nrm));
+                if ((rc = sigma(Vk(0), Sk(0)))) return rc;
+                FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
+                if ((rc = add_column(0))) return rc;
+                k = 1;
+                FCI_CUDA(h, cudaMemcpyAsync(w.cp, w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                have_prev = true;
+                E_prev = lam;
+                continue;
+            }
+        } else if (rn <= o->tol_residual && it > 1 && fabs(dE) <= o->tol_energy) {
+            converged = true;
+            E_prev = lam;
+            break;
+        }
+        if (o->eps > 0.0) {
+            if (cplx) k_threshold<true><<<vb, RED_THREADS, 0, s>>>(w.t, n, scal, o->eps);
+            else k_threshold<false><<<vb, RED_THREADS, 0, s>>>(w.t, n, scal, o->eps);
+        }
+        if (k >= ms) {
+            // collapse to the current and previous Ritz vectors (sigma by linearity)
+            FCI_CUDA(h, cudaMemcpyAsync(Vk(0), w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            FCI_CUDA(h, cudaMemcpyAsync(Sk(0), w.sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            int knew = 1;
+            if (have_prev && ms > 2) {
+                // p = c_prev - <c|c_prev> c, S_p = sc_prev - <c|c_prev> sc, both / ||p||
+                FCI_CUDA(h, multidot(w.c, 1, w.cp, dots));
+                FCI_CUDA(h, cudaMemcpyAsync(Vk(1), w.cp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                FCI_CUDA(h, cudaMemcpyAsync(Sk(1), w.scp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                k_negate<<<1, 64, 0, s>>>(dots, 1);
+                FCI_CUDA(h, lincomb(w.c, 1, dots, 1.0, Vk(1), 1));
+                FCI_CUDA(h, lincomb(w.sc, 1, dots, 1.0, Sk(1), 1));
+                k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, partial);
+                k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+                double pn2 = 0.0;
+                FCI_CUDA(h, cudaMemcpyAsync(&pn2, nrm, 8, cudaMemcpyDeviceToHost, s));
+                FCI_CUDA(h, cudaStreamSynchronize(s));
+                if (sqrt(pn2) > 1e-10) {
+                    k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, nrm);
+                    k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(1), nreal, nrm);
+                    knew = 2;
+                }
+            }
+            FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
+            for (int j = 0; j < knew; ++j)
+                if ((rc = add_column(j))) return rc;
+            k = knew;
+        }
+        // two rounds of classical Gram-Schmidt against V[0..k)
+        for (int round = 0; round < 2; ++round) {
+            FCI_CUDA(h, multidot(w.V, k, w.t, dots));
+            k_negate<<<1, 64, 0, s>>>(dots, k);
+            FCI_CUDA(h, lincomb(w.V, k, dots, 1.0, w.t, 1));
+        }
+        k_norm2<<<vb, RED_THREADS, 0, s>>>(w.t, nreal, partial);
+        k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+        double tn2 = 0.0;
+        FCI_CUDA(h, cudaMemcpyAsync(&tn2, nrm, 8, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(h, cudaMemcpyAsync(w.cp, w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+        FCI_CUDA(h, cudaMemcpyAsync(w.scp, w.sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+        FCI_CUDA(h, cudaStreamSynchronize(s));
+        have_prev = true;
+        E_prev = lam;
+        if (!(sqrt(tn2) >= 1e-10)) break;  // new direction linearly dependent on the subspace
+        k_scale<<<vb, RED_THREADS, 0, s>>>(w.t, nreal, nrm);
+        FCI_CUDA(h, cudaMemcpyAsync(Vk(k), w.t, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+        if ((rc = sigma(Vk(k), Sk(k)))) return rc;
+        if ((rc = add_column(k))) return rc;
+        ++k;
+    }
+    FCI_CUDA(h, cudaMemcpyAsync(C_io, w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+    FCI_CUDA(h, cudaStreamSynchronize(s));
+    *energy = E_prev + h->e_core;
+    if (log) {
+        log->n_iter = std::min(it_rec, log->capacity);
+        log->converged = converged ? 1 : 0;
+        log->n_sigma = n_sigma;
+    }
+    if (!converged) return fci_fail(h, FCI_ERR_NOT_CONVERGED, "Davidson did not converge in %d iterations", o->max_iter);
+    return FCI_OK;
+}

@@ -1,0 +1,285 @@
+"""Python binding of libfci (include/fci.h): argument marshalling only.
+
+Every step of the sigma build and of Davidson runs in the CUDA library; this module
+turns numpy/torch objects into pointers and sizes, allocates caller-owned device
+buffers with torch, and raises on error codes.  If libfci.so is missing it raises at
+import: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfci.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(the CUDA library is the only implementation)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+FCI_OK, FCI_ERR_ARG, FCI_ERR_OOM, FCI_ERR_CUDA, FCI_ERR_NOT_CONVERGED, FCI_ERR_TIMEOUT, \
+    FCI_ERR_UNSUPPORTED, FCI_ERR_STATE = range(8)
+FCI_R64, FCI_C128 = 0, 1
+FCI_MODE_NONE, FCI_MODE_FCI, FCI_MODE_SPINOR, FCI_MODE_DAS = range(4)
+FCI_PREC_FP64, FCI_PREC_OZ_BF16 = 0, 1
+PRECISIONS = {"fp64": FCI_PREC_FP64, "oz_bf16": FCI_PREC_OZ_BF16}
+TABLES = {"strings_alpha": 0, "strings_beta": 1, "repl_alpha": 2, "repl_beta": 3,
+          "das_categories": 4, "das_address": 5}
+
+_vp, _i32, _i64, _dbl, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+
+
+class fci_info(ctypes.Structure):
+    _fields_ = [("mode", _i32), ("dtype", _i32), ("n_orb", _i32), ("n_alpha", _i32), ("n_beta", _i32),
+                ("n_pair", _i32), ("n_ent_alpha", _i32), ("n_ent_beta", _i32),
+                ("n_str_alpha", _i64), ("n_str_beta", _i64), ("n_det", _i64),
+                ("n_det_intermediate", _i64), ("n_categories", _i32), ("n_categories_intermediate", _i32)]
+
+
+class fci_davidson_opts(ctypes.Structure):
+    _fields_ = [("max_iter", _i32), ("max_subspace", _i32), ("tol_residual", _dbl), ("tol_energy", _dbl),
+                ("eps", _dbl), ("precision", _i32), ("n_slices", _i32), ("switch_residual", _dbl),
+                ("use_guess", _i32)]
+
+
+class fci_davidson_iter(ctypes.Structure):
+    _fields_ = [("iteration", _i32), ("precision", _i32), ("energy", _dbl), ("delta_energy", _dbl),
+                ("max_delta_c", _dbl), ("residual_norm", _dbl), ("seconds", _dbl)]
+
+
+class fci_davidson_log(ctypes.Structure):
+    _fields_ = [("n_iter", _i32), ("converged", _i32), ("n_sigma", _i32), ("capacity", _i32),
+                ("iters", ctypes.POINTER(fci_davidson_iter))]
+
+
+def _sig(name, args, res=_i32):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_create = _sig("fci_create", [ctypes.POINTER(_vp), _i32])
+_destroy = _sig("fci_destroy", [_vp])
+_last_error = _sig("fci_last_error", [_vp], ctypes.c_char_p)
+_get_info = _sig("fci_get_info", [_vp, ctypes.POINTER(fci_info)])
+_count = _sig("fci_count_determinants", [_i32, _i32, _i32], _i64)
+_setup = _sig("fci_setup_integrals", [_vp, _i32, _i32, _vp, _vp, _dbl, _vp])
+_strings = _sig("fci_build_strings", [_vp, _i32, _i32, _vp])
+_das = _sig("das_build_categories", [_vp, _i32, _vp, _vp, _vp, _i32, _vp])
+_diag = _sig("fci_diagonal", [_vp, _vp, _vp])
+_ws = _sig("fci_sigma_workspace_bytes", [_vp, _i32, _i32, _i32, ctypes.POINTER(_sz)])
+_sigma = _sig("fci_sigma", [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _sz, _vp])
+_dav_defaults = _sig("fci_davidson_default_opts", [ctypes.POINTER(fci_davidson_opts)], None)
+_dav_ws = _sig("fci_davidson_workspace_bytes", [_vp, ctypes.POINTER(fci_davidson_opts), ctypes.POINTER(_sz)])
+_davidson = _sig("davidson_solve", [_vp, ctypes.POINTER(fci_davidson_opts), _vp, ctypes.POINTER(_dbl),
+                                    ctypes.POINTER(fci_davidson_log), _vp, _sz, _vp])
+_tbytes = _sig("fci_table_bytes", [_vp, _i32, ctypes.POINTER(_sz)])
+_tcopy = _sig("fci_copy_table", [_vp, _i32, _vp, _sz, _vp])
+_set_timing = _sig("fci_set_phase_timing", [_vp, _i32])
+_get_times = _sig("fci_get_phase_times", [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), _i32])
+PHASES = ("gather", "contract", "scatter", "other")
+
+
+class FCIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libfci error {code}: {msg}")
+        self.code = code
+
+
+def count_determinants(n_orb: int, n_alpha: int, n_beta: int) -> int:
+    return int(_count(n_orb, n_alpha, n_beta))
+
+
+def last_error(h=None) -> str:
+    return (_last_error(h) or b"").decode()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return _vp(s.cuda_stream)
+
+
+def _alloc(nbytes: int, device) -> torch.Tensor:
+    """Caller-owned device buffer (torch allocator), 256-byte aligned."""
+    return torch.empty(max(int(nbytes), 1) + 256, dtype=torch.uint8, device=device)
+
+
+def _aligned_ptr(buf: torch.Tensor) -> int:
+    p = buf.data_ptr()
+    return (p + 255) & ~255
+
+
+@dataclass
+class DavidsonResult:
+    energy: float
+    vector: torch.Tensor
+    converged: bool
+    n_sigma: int
+    iterations: list
+
+
+class FCI:
+    """One problem on one GPU: integrals, strings (FCI, spinor or DAS layout)."""
+
+    def __init__(self, device: int = 0):
+        self.device = torch.device("cuda", device)
+        h = _vp()
+        rc = _create(ctypes.byref(h), device)
+        if rc:
+            raise FCIError(rc, last_error(None))
+        self._h = h
+        self._ws = None
+        self._ws_ptr = 0
+        self._ws_bytes = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise FCIError(rc, last_error(self._h))
+
+    # -------------------------------------------------------------- setup
+    def setup_integrals(self, h1: np.ndarray, g2: np.ndarray, e_core: float = 0.0):
+        cplx = np.iscomplexobj(h1) or np.iscomplexobj(g2)
+        dt = np.complex128 if cplx else np.float64
+        self._h1 = np.ascontiguousarray(h1, dt)
+        self._g2 = np.ascontiguousarray(g2, dt)
+        n = self._h1.shape[0]
+        self._check(_setup(self._h, n, FCI_C128 if cplx else FCI_R64, self._h1.ctypes.data,
+                           self._g2.ctypes.data, float(e_core), _stream()))
+        return self
+
+    def build_strings(self, n_alpha: int, n_beta: int = -1):
+        self._check(_strings(self._h, n_alpha, n_beta, _stream()))
+        return self
+
+    def build_das(self, orbs_per_space, ref_alpha, ref_beta, max_transfer: int):
+        S = len(orbs_per_space)
+        o = (ctypes.c_int * S)(*orbs_per_space)
+        a = (ctypes.c_int * S)(*ref_alpha)
+        b = (ctypes.c_int * S)(*ref_beta)
+        self._check(_das(self._h, S, o, a, b, max_transfer, _stream()))
+        return self
+
+    @property
+    def info(self) -> dict:
+        inf = fci_info()
+        self._check(_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in fci_info._fields_}
+
+    @property
+    def is_complex(self) -> bool:
+        return self.info["dtype"] == FCI_C128
+
+    @property
+    def n_det(self) -> int:
+        return self.info["n_det"]
+
+    def vector_dtype(self):
+        return torch.complex128 if self.is_complex else torch.float64
+
+    # ------------------------------------------------------------ compute
+    def diagonal(self, stream=None) -> torch.Tensor:
+        out = torch.empty(self.n_det, dtype=torch.float64, device=self.device)
+        self._check(_diag(self._h, out.data_ptr(), _stream(stream)))
+        return out
+
+    def sigma_workspace_bytes(self, precision="fp64", n_slices=0, n_vec=1) -> int:
+        b = _sz()
+        self._check(_ws(self._h, n_vec, PRECISIONS[precision], n_slices, ctypes.byref(b)))
+        return b.value
+
+    def _workspace(self, nbytes: int):
+        if self._ws is None or self._ws_bytes < nbytes:
+            self._ws = None
+            self._ws = _alloc(nbytes, self.device)
+            self._ws_ptr = _aligned_ptr(self._ws)
+            self._ws_bytes = nbytes
+        return self._ws_ptr, self._ws_bytes
+
+    def sigma(self, C: torch.Tensor, precision: str = "fp64", n_slices: int = 0, out: torch.Tensor = None,
+              stream=None) -> torch.Tensor:
+        """sigma = H C.  C: (n_det,) or (n_vec, n_det) on the device, or on the host
+        (then copied in and the result copied back, both inside this call)."""
+        host = C.device.type == "cpu"
+        Cd = C.to(self.device, non_blocking=True) if host else C
+        Cd = Cd.contiguous()
+        if Cd.dtype != self.vector_dtype():
+            raise TypeError(f"C must be {self.vector_dtype()}")
+        n_vec = 1 if Cd.dim() == 1 else Cd.shape[0]
+        if Cd.shape[-1] != self.n_det:
+            raise ValueError("C has the wrong length")
+        res = torch.empty_like(Cd) if (out is None or host) else out
+        p, nb = self._workspace(self.sigma_workspace_bytes(precision, n_slices, n_vec))
+        self._check(_sigma(self._h, Cd.data_ptr(), res.data_ptr(), n_vec, PRECISIONS[precision], n_slices,
+                           p, nb, _stream(stream)))
+        if host:
+            dst = out if out is not None else torch.empty_like(C, pin_memory=C.is_pinned())
+            dst.copy_(res, non_blocking=False)
+            return dst
+        return res
+
+    def davidson(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
+                 precision="fp64", n_slices=6, switch_residual=1e-5, guess: torch.Tensor = None,
+                 stream=None) -> DavidsonResult:
+        o = fci_davidson_opts()
+        _dav_defaults(ctypes.byref(o))
+        o.max_iter, o.max_subspace = max_iter, max_subspace
+        o.tol_residual, o.tol_energy, o.eps = tol_residual, tol_energy, eps
+        o.precision, o.n_slices, o.switch_residual = PRECISIONS[precision], n_slices, switch_residual
+        o.use_guess = 1 if guess is not None else 0
+        b = _sz()
+        self._check(_dav_ws(self._h, ctypes.byref(o), ctypes.byref(b)))
+        p, nb = self._workspace(b.value)
+        C = (guess.to(self.device).clone() if guess is not None
+             else torch.zeros(self.n_det, dtype=self.vector_dtype(), device=self.device))
+        cap = max_iter + 2
+        iters = (fci_davidson_iter * cap)()
+        log = fci_davidson_log(0, 0, 0, cap, ctypes.cast(iters, ctypes.POINTER(fci_davidson_iter)))
+        E = _dbl()
+        rc = _davidson(self._h, ctypes.byref(o), C.data_ptr(), ctypes.byref(E), ctypes.byref(log), p, nb,
+                       _stream(stream))
+        if rc not in (FCI_OK, FCI_ERR_NOT_CONVERGED):
+            self._check(rc)
+        its = [{k: getattr(iters[i], k) for k, _ in fci_davidson_iter._fields_} for i in range(log.n_iter)]
+        return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its)
+
+    # ------------------------------------------------------------- timing
+    def set_phase_timing(self, enable: bool = True):
+        self._check(_set_timing(self._h, 1 if enable else 0))
+
+    def phase_times(self, reset: bool = True) -> dict:
+        ms = (_dbl * 4)()
+        nl = (_i64 * 4)()
+        self._check(_get_times(self._h, ms, nl, 1 if reset else 0))
+        return {p: {"ms": ms[i], "launches": nl[i]} for i, p in enumerate(PHASES)}
+
+    # ------------------------------------------------------------- tables
+    def table(self, name: str) -> torch.Tensor:
+        t = TABLES[name]
+        b = _sz()
+        self._check(_tbytes(self._h, t, ctypes.byref(b)))
+        if b.value == 0:
+            raise FCIError(FCI_ERR_STATE, f"table {name} does not exist in this layout")
+        dt = {0: torch.int64, 1: torch.int64, 2: torch.int32, 3: torch.int32, 4: torch.int64, 5: torch.int64}[t]
+        out = torch.empty(b.value // torch.tensor([], dtype=dt).element_size(), dtype=dt, device=self.device)
+        self._check(_tcopy(self._h, t, out.data_ptr(), b.value, _stream()))
+        torch.cuda.current_stream().synchronize()
+        return out
