@@ -167,8 +167,12 @@ typedef struct {
     int precision;          /* FCI_PREC_* used for sigma in the first phase */
     int n_slices;           /* slices for FCI_PREC_OZ_BF16 */
     double switch_residual; /* mixed mode: once ||r|| <= this, restart from the Ritz
-                               vector with FP64 sigma (default 1e-5) */
+                               vector with the final precision (default 1e-5) */
     int use_guess;          /* 1: start from C_io; 0: unit vector at min H_II */
+    int final_precision;    /* sigma after the switch: FCI_PREC_FP64 (default), or
+                               FCI_PREC_OZ_BF16 with final_slices >= 6 (error below
+                               1e-11 of ||sigma||, the FP64 parity bar) */
+    int final_slices;
 } fci_davidson_opts;
 
 typedef struct {
@@ -227,6 +231,11 @@ int fci_table_bytes(fci_handle h, int table, size_t *bytes);
 /* Copy a table into a caller DEVICE buffer of at least fci_table_bytes bytes. */
 int fci_copy_table(fci_handle h, int table, void *dst, size_t bytes, fci_stream stream);
 
+
+/* Synchronise `stream` and report device-side failures of earlier calls on h: returns
+ * FCI_ERR_TIMEOUT if a bounded wait inside a split-precision kernel expired (its sigma
+ * output was then filled with NaN), else FCI_OK.  Clears the recorded status. */
+int fci_sync_status(fci_handle h, fci_stream stream);
 
 /* ------------------------------------------------------------ phase timing */
 

@@ -22,7 +22,7 @@ constexpr int RED_THREADS = 256;
 constexpr int KMAX = 32;
 
 struct dav_scalars {      // device-resident scalars, read back each iteration
-    double lam;           // lowest Ritz value (without e_core)
+    double lam;           // lowest Ritz value (sigma carries e_core C, so e_core is included)
     double rnorm2, snorm2, maxdc;
     double ov_re, ov_im;  // <c_prev|c>
     double tnorm2;
@@ -379,7 +379,7 @@ size_t davidson_ws_bytes(const fci_context *h, const fci_davidson_opts *o) {
     const size_t esz = h->dtype == FCI_C128 ? 16 : 8;
     const size_t vec = al((size_t)n * esz);
     size_t sig = sigma_ws_bytes(h, o->precision, o->n_slices);
-    if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, FCI_PREC_FP64, 0));
+    if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, o->final_precision, o->final_slices));
     return 2 * (size_t)o->max_subspace * vec + 5 * vec + al((size_t)n * 8) + al(sig);
 }
 
@@ -404,7 +404,7 @@ int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, doubl
     w.diag = (double *)p; p += al((size_t)n * 8);
     w.sig_ws = p;
     size_t sig = sigma_ws_bytes(h, o->precision, o->n_slices);
-    if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, FCI_PREC_FP64, 0));
+    if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, o->final_precision, o->final_slices));
     w.sig_bytes = al(sig);
     const int64_t ldv = (int64_t)(vec / esz);  // elements between consecutive subspace vectors
 
@@ -440,10 +440,12 @@ int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, doubl
     auto Vk = [&](int i) { return (double *)((char *)w.V + (size_t)i * vec); };
     auto Sk = [&](int i) { return (double *)((char *)w.S + (size_t)i * vec); };
     int n_sigma = 0;
-    int prec = o->precision;
+    int prec = o->precision, slices = o->n_slices;
+    bool final_phase = o->precision == FCI_PREC_FP64 ||
+                       (o->precision == o->final_precision && o->n_slices == o->final_slices);
     auto sigma = [&](const double *x, double *out) -> int {
         ++n_sigma;
-        return sigma_dispatch(h, x, out, prec, o->n_slices, w.sig_ws, w.sig_bytes, s);
+        return sigma_dispatch(h, x, out, prec, slices, w.sig_ws, w.sig_bytes, s);
     };
     // New subspace column k: Hs[:, k] = V^H S_k.
     auto add_column = [&](int k) -> int {
@@ -502,7 +504,7 @@ int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, doubl
             fci_davidson_iter &r = log->iters[it_rec];
             r.iteration = it;
             r.precision = prec;
-            r.energy = lam + h->e_core;
+            r.energy = lam;  // sigma already includes e_core C
             r.delta_energy = dE;
             r.max_delta_c = have_prev ? hs.maxdc : 0.0;
             r.residual_norm = rn;
@@ -510,11 +512,13 @@ int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, doubl
         }
         ++it_rec;
         if (!isfinite(lam) || !isfinite(rn)) return fci_fail(h, FCI_ERR_CUDA, "Davidson produced a non-finite value");
-        if (prec != FCI_PREC_FP64) {
+        if (!final_phase) {
             ++phase1_iters;
             if (rn <= o->switch_residual || phase1_iters >= o->max_iter / 2) {
-                // Residual correction: restart from the Ritz vector with FP64 sigma.
-                prec = FCI_PREC_FP64;
+                // Residual correction: restart from the Ritz vector with the final precision.
+                final_phase = true;
+                prec = o->final_precision;
+                slices = o->final_slices;
                 FCI_CUDA(h, cudaMemcpyAsync(Vk(0), w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
                 FCI_CUDA(h, normalize(Vk(0), nrm));
                 if ((rc = sigma(Vk(0), Sk(0)))) return rc;
@@ -537,17 +541,27 @@ int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, doubl
         }
         if (k >= ms) {
             // collapse to the current and previous Ritz vectors (sigma by linearity)
+            // V_0 = c / ||c||, S_0 = sc / ||c||
             FCI_CUDA(h, cudaMemcpyAsync(Vk(0), w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
             FCI_CUDA(h, cudaMemcpyAsync(Sk(0), w.sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, partial);
+            k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+            k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, nrm);
+            k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(0), nreal, nrm);
             int knew = 1;
             if (have_prev && ms > 2) {
                 // p = c_prev - <c|c_prev> c, S_p = sc_prev - <c|c_prev> sc, both / ||p||
-                FCI_CUDA(h, multidot(w.c, 1, w.cp, dots));
+                // Two Gram-Schmidt passes: c and c_prev are nearly parallel near convergence,
+                // and one pass leaves an orthogonality error of eps / ||p|| that compounds
+                // over successive collapses.
                 FCI_CUDA(h, cudaMemcpyAsync(Vk(1), w.cp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
                 FCI_CUDA(h, cudaMemcpyAsync(Sk(1), w.scp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-                k_negate<<<1, 64, 0, s>>>(dots, 1);
-                FCI_CUDA(h, lincomb(w.c, 1, dots, 1.0, Vk(1), 1));
-                FCI_CUDA(h, lincomb(w.sc, 1, dots, 1.0, Sk(1), 1));
+                for (int pass = 0; pass < 2; ++pass) {
+                    FCI_CUDA(h, multidot(Vk(0), 1, Vk(1), dots));
+                    k_negate<<<1, 64, 0, s>>>(dots, 1);
+                    FCI_CUDA(h, lincomb(Vk(0), 1, dots, 1.0, Vk(1), 1));
+                    FCI_CUDA(h, lincomb(Sk(0), 1, dots, 1.0, Sk(1), 1));
+                }
                 k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, partial);
                 k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
                 double pn2 = 0.0;
@@ -588,7 +602,7 @@ int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, doubl
     }
     FCI_CUDA(h, cudaMemcpyAsync(C_io, w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
     FCI_CUDA(h, cudaStreamSynchronize(s));
-    *energy = E_prev + h->e_core;
+    *energy = E_prev;
     if (log) {
         log->n_iter = std::min(it_rec, log->capacity);
         log->converged = converged ? 1 : 0;

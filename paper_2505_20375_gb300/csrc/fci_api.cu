@@ -193,6 +193,21 @@ int fci_get_phase_times(fci_handle h, double *ms, int64_t *launches, int reset) 
     return FCI_OK;
 }
 
+int fci_sync_status(fci_handle h, fci_stream stream) {
+    if (!h) return fci_fail(nullptr, FCI_ERR_ARG, "NULL handle");
+    int rc = set_dev(h);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    FCI_CUDA(h, cudaStreamSynchronize(s));
+    if (!h->last_status) return FCI_OK;
+    int st = 0;
+    FCI_CUDA(h, cudaMemcpy(&st, h->last_status, sizeof st, cudaMemcpyDeviceToHost));
+    FCI_CUDA(h, cudaMemset(h->last_status, 0, sizeof st));
+    if (st == FCI_ERR_TIMEOUT) return fci_fail(h, FCI_ERR_TIMEOUT, "a bounded device wait expired; sigma was set to NaN");
+    if (st) return fci_fail(h, st, "device status %d", st);
+    return FCI_OK;
+}
+
 int fci_destroy(fci_handle h) {
     if (!h) return FCI_OK;
     cudaSetDevice(h->device);
@@ -472,6 +487,8 @@ void fci_davidson_default_opts(fci_davidson_opts *o) {
     o->n_slices = 6;
     o->switch_residual = 1e-5;
     o->use_guess = 0;
+    o->final_precision = FCI_PREC_FP64;
+    o->final_slices = 0;
 }
 
 static int check_opts(fci_context *h, const fci_davidson_opts *o) {
@@ -484,6 +501,10 @@ static int check_opts(fci_context *h, const fci_davidson_opts *o) {
         return fci_fail(h, FCI_ERR_ARG, "unknown precision %d", o->precision);
     if (o->precision == FCI_PREC_OZ_BF16 && (o->n_slices < 2 || o->n_slices > 8))
         return fci_fail(h, FCI_ERR_ARG, "n_slices %d outside [2, 8]", o->n_slices);
+    if (o->final_precision != FCI_PREC_FP64 && o->final_precision != FCI_PREC_OZ_BF16)
+        return fci_fail(h, FCI_ERR_ARG, "unknown final precision %d", o->final_precision);
+    if (o->final_precision == FCI_PREC_OZ_BF16 && (o->final_slices < 6 || o->final_slices > 8))
+        return fci_fail(h, FCI_ERR_ARG, "final_slices %d outside [6, 8]", o->final_slices);
     return FCI_OK;
 }
 
@@ -503,7 +524,7 @@ int davidson_solve(fci_handle h, const fci_davidson_opts *o, void *C_io, double 
     if (rc) return rc;
     if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "no strings built");
     if (!C_io || !energy) return fci_fail(h, FCI_ERR_ARG, "NULL C_io/energy");
-    if (o->precision == FCI_PREC_OZ_BF16 && h->dtype != FCI_R64)
+    if ((o->precision == FCI_PREC_OZ_BF16 || o->final_precision == FCI_PREC_OZ_BF16) && h->dtype != FCI_R64)
         return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real integrals only");
     const size_t need = davidson_ws_bytes(h, o);
     if (ws_bytes < need || !ws) return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes", ws_bytes, need);

@@ -105,6 +105,9 @@ struct fci_context {
     double phase_ms[FCI_N_PHASES] = {0, 0, 0, 0};
     int64_t phase_launches[FCI_N_PHASES] = {0, 0, 0, 0};
 
+    // device status word of the last split-precision sigma (inside the caller's workspace)
+    int *last_status = nullptr;
+
     // scratch for reductions (small)
     double *d_small = nullptr;
     size_t small_bytes = 0;

@@ -1,8 +1,581 @@
-// Split-precision (Ozaki) contraction on tcgen05 tensor cores (filled in below).
+// Split-precision contraction E = G D on the 5th-generation tensor cores (tcgen05),
+// Ozaki style, for alpha/beta strings with real pair-packed integrals.
+//
+// Both operands go to fixed point with one exponent each (C and hence D by
+// 2^{sh_C}, G by 2^{sh_G}) and are cut into s signed base-256 digits in [-128, 127]:
+//   X_int = sum_{j<s} x_j 256^j.
+// Digits are exact in bf16, products of two digits are below 2^14, and every partial
+// sum of the MMA stays an integer below 2^24, so the FP32 accumulation in TMEM is exact.
+// The product is regrouped by significance level L = i + j of the digit pair; only the
+// top s levels (L >= s - 1) are formed (the usual triangular truncation), each into its
+// own TMEM accumulator:
+//   S_L = sum_{i+j=L} G_i D_j,     G_int D_int ~ sum_L S_L 256^L.
+// The epilogue turns the exact level sums into one int64 per element (levels below L0
+// rounded away, L0 = max(s-1, 2s-6) keeps |E_int| < 2^54) and writes E_int; the scatter
+// sums E_int values exactly in int64 and converts once:
+//   sigma_I = 2^{8 L0 - sh_G - sh_C} sum <I|E_pq|K> E_int[pq, K] + e_core C_I.
+// (Methods, Eqs. sigmaL/sigmaL2e: E = g' D is the dense contraction of the sigma build.)
+//
+// Kernel layout (one persistent CTA per SM, 288 threads):
+//   warps 0-3  producers: gather D_int for a tile of 32 determinants from the fixed-point
+//              C and the pair tables, keep it in registers, and write its s digit planes
+//              (bf16, canonical K-major core-matrix layout) into a 3-slot shared ring;
+//   warps 4-7  epilogue: read the s level accumulators of a tile from TMEM (one warp per
+//              32-lane quadrant), combine them in int64, store E_int rows;
+//   warp 8     allocates TMEM; lane 0 issues tcgen05.mma (M = 128 pair rows of G digits
+//              resident in shared memory, N = 32 determinants, K = 16 per instruction) and
+//              tcgen05.commit to the mbarriers that hand buffers between the roles.
+// Level accumulators are double-buffered (2 x s x 32 TMEM columns).  Every wait on an
+// mbarrier is bounded in time; on expiry the kernel records FCI_ERR_TIMEOUT in a device
+// status word, stops issuing work, drains the MMAs it issued, frees TMEM and returns.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+
 #include "fci_internal.h"
 
-int oz_prepare_G(fci_context *h, int) { return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision not built yet"); }
-size_t oz_workspace_bytes(const fci_context *, int) { return 0; }
-int oz_sigma_fci(fci_context *h, const double *, double *, int, void *, size_t, cudaStream_t) {
-    return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision not built yet");
+namespace {
+
+constexpr int OZ_THREADS = 288;
+constexpr int OZ_NT = 32;   // determinants per tile (MMA N)
+constexpr int OZ_RING = 3;  // digit-plane slots
+constexpr int OZ_MAXS = 7;
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, bf16 inputs, fp32 accumulate.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle (canonical K-major core matrices of
+// 8 rows x 16 bytes): lbo = byte stride between core matrices along K, sbo = byte
+// stride between 8-row groups along M/N.  Version field 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// bf16 bits of the integer d in [-128, 127] (exact): 2^23 + 2^22 + d in fp32, minus
+// the offset, keeps all 8 significant bits in the upper half of the fp32 word.
+__device__ __forceinline__ uint32_t digit_f32(uint32_t byte) {
+    const float f = __uint_as_float(0x4B3FFF80u + byte) - 12582912.0f;
+    return __float_as_uint(f);
+}
+
+struct OzParams {
+    int64_t N, nsa, nsb;
+    int npair, KC, s, L0, g_slice_bytes;
+    const int32_t *pairA, *pairB;
+    const int64_t *Cint;
+    const uint4 *Gimg;
+    int64_t *E;
+    int64_t ldE;
+    int *status;
+    long long timeout_cycles;
+    int stall_test;
+};
+
+// Warp-uniform variant: lane 0 waits, every lane gets the same answer, so no lane can
+// leave a loop that the others continue (the tcgen05.ld/alloc forms are .sync.aligned).
+__device__ __forceinline__ bool oz_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                             long long timeout);
+
+struct OzShared {  // lives after the operand buffers
+    uint64_t plane_full[OZ_RING], plane_empty[OZ_RING];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// Bounded wait: returns false on timeout or when another role has aborted.
+__device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                        long long timeout) {
+    const long long t0 = clock64();
+    int spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if (((++spins) & 63) == 0) {
+            if (*abort) return false;
+            if (clock64() - t0 > timeout) {
+                *abort = 1;
+                atomicExch(status, FCI_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool oz_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                             long long timeout) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = oz_wait(bar, parity, abort, status, timeout) ? 1 : 0;
+    return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
+    extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
+    const int s = p.s, KC = p.KC;
+    const int plane_bytes = OZ_NT * KC * 16;
+    uint8_t *sG = smem;
+    uint8_t *sRing = sG + (size_t)s * p.g_slice_bytes;
+    OzShared *sh = (OzShared *)(sRing + OZ_RING * plane_bytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // G digit slices: one copy per CTA, reused for every tile
+    {
+        const int n16 = s * p.g_slice_bytes / 16;
+        uint4 *dst = (uint4 *)sG;
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(p.Gimg + i);
+    }
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < OZ_RING; ++r) {
+            mbar_init(smem_u32(&sh->plane_full[r]), 4);
+            mbar_init(smem_u32(&sh->plane_empty[r]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&sh->acc_full[b]), 1);
+            mbar_init(smem_u32(&sh->acc_empty[b]), 4);
+        }
+        mbar_init(smem_u32(&sh->drain), 1);
+        sh->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 8) {
+        tmem_alloc(smem_u32(&sh->tmem_base), 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort = &sh->abort;
+    const int64_t ntiles = (p.N + OZ_NT - 1) / OZ_NT;
+
+    if (warp < 4) {
+        // ---------------------------------------------------------------- producers
+        const int t = threadIdx.x;  // 0..127
+        const int units = OZ_NT * KC;
+        uint32_t q = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            int64_t dint[4][8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int unit = t + 128 * u;
+                const int r = unit % OZ_NT, c = unit / OZ_NT;
+                const int64_t det = tile * OZ_NT + r;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) dint[u][e] = 0;
+                if (unit < units && det < p.N) {
+                    const int64_t ka = det / p.nsb, kb = det - ka * p.nsb;
+                    const int64_t *Crow = p.Cint + ka * p.nsb;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int rs = 8 * c + e;
+                        if (rs < p.npair) {
+                            int64_t v = 0;
+                            const int32_t ea = __ldg(p.pairA + (int64_t)rs * p.nsa + ka);
+                            if (ea >= 0) {
+                                const int64_t x = __ldg(p.Cint + (int64_t)(ea >> 1) * p.nsb + kb);
+                                v = (ea & 1) ? -x : x;
+                            }
+                            const int32_t eb = __ldg(p.pairB + (int64_t)rs * p.nsb + kb);
+                            if (eb >= 0) {
+                                const int64_t x = __ldg(Crow + (eb >> 1));
+                                v += (eb & 1) ? -x : x;
+                            }
+                            dint[u][e] = v;
+                        }
+                    }
+                }
+            }
+            // biased digits: Y = D_int + sum_j 128 256^j, digit_j = byte_j(Y) - 128
+            uint64_t bias = 0;
+            for (int j = 0; j < s; ++j) bias |= (uint64_t)0x80 << (8 * j);
+            for (int j = s - 1; j >= 0; --j, ++q) {
+                const int slot = q % OZ_RING;
+                const uint32_t use = q / OZ_RING;
+                if (use > 0 && !oz_wait_warp(smem_u32(&sh->plane_empty[slot]), (use - 1) & 1, abort, p.status,
+                                             p.timeout_cycles))
+                    goto producer_done;
+                uint8_t *plane = sRing + slot * plane_bytes;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int unit = t + 128 * u;
+                    if (unit >= units) continue;
+                    const int r = unit % OZ_NT, c = unit / OZ_NT;
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        const uint64_t y0 = (uint64_t)dint[u][e] + bias, y1 = (uint64_t)dint[u][e + 1] + bias;
+                        const uint32_t f0 = digit_f32((uint32_t)(y0 >> (8 * j)) & 0xFFu);
+                        const uint32_t f1 = digit_f32((uint32_t)(y1 >> (8 * j)) & 0xFFu);
+                        w[e / 2] = __byte_perm(f0, f1, 0x7632);
+                    }
+                    const uint32_t off = (uint32_t)(((r >> 3) * KC + c) * 128 + (r & 7) * 16);
+                    *(uint4 *)(plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0 && !p.stall_test) mbar_arrive(smem_u32(&sh->plane_full[slot]));
+            }
+        }
+    producer_done:;
+    } else if (warp < 8) {
+        // ---------------------------------------------------------------- epilogue
+        const int qd = warp - 4;  // TMEM lane quadrant: rows 32 qd .. 32 qd + 31
+        const int row = 32 * qd + lane;
+        const int lowshift = 8 * (p.L0 - (s - 1));
+        uint32_t tau = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
+            const int buf = tau & 1;
+            if (!oz_wait_warp(smem_u32(&sh->acc_full[buf]), (tau >> 1) & 1, abort, p.status, p.timeout_cycles))
+                break;
+            tc_fence_after();
+            int64_t acc[OZ_NT];
+#pragma unroll
+            for (int c = 0; c < OZ_NT; ++c) acc[c] = 0;
+            for (int L = s - 1; L <= 2 * s - 2; ++L) {
+                uint32_t v[32];
+                const uint32_t col = (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT);
+                tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + col, v);
+                tmem_ld_wait();
+                if (L < p.L0) {
+                    const int sh8 = 8 * (L - (s - 1));
+#pragma unroll
+                    for (int c = 0; c < OZ_NT; ++c)
+                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << sh8);
+                } else {
+                    if (L == p.L0 && lowshift > 0) {
+                        const int64_t half = (int64_t)1 << (lowshift - 1);
+#pragma unroll
+                        for (int c = 0; c < OZ_NT; ++c) acc[c] = (acc[c] + half) >> lowshift;
+                    }
+                    const int sh8 = 8 * (L - p.L0);
+#pragma unroll
+                    for (int c = 0; c < OZ_NT; ++c)
+                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << sh8);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
+            if (row < p.npair) {
+                const int64_t d0 = tile * OZ_NT;
+                int64_t *dst = p.E + (int64_t)row * p.ldE + d0;
+                if (d0 + OZ_NT <= p.N) {
+#pragma unroll
+                    for (int c = 0; c < OZ_NT; c += 2)
+                        *(longlong2 *)(dst + c) = make_longlong2(acc[c], acc[c + 1]);
+                } else {
+                    for (int c = 0; c < OZ_NT; ++c)
+                        if (d0 + c < p.N) dst[c] = acc[c];
+                }
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        const uint32_t idesc = idesc_bf16(128, OZ_NT);
+        const uint32_t sbo = (uint32_t)(KC * 128);
+        const uint32_t g0 = smem_u32(sG), r0 = smem_u32(sRing);
+        uint32_t q = 0, tau = 0;
+        bool issued = false;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
+            const int buf = tau & 1;
+            if (tau >= 2 && !oz_wait(smem_u32(&sh->acc_empty[buf]), ((tau >> 1) - 1) & 1, abort, p.status,
+                                     p.timeout_cycles))
+                break;
+            tc_fence_after();
+            bool ok = true;
+            for (int j = s - 1; j >= 0; --j, ++q) {
+                const int slot = q % OZ_RING;
+                if (!oz_wait(smem_u32(&sh->plane_full[slot]), (q / OZ_RING) & 1, abort, p.status,
+                             p.timeout_cycles)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int i = s - 1 - j; i < s; ++i) {
+                    const int L = i + j;
+                    const uint32_t d = tmem + (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT);
+                    for (int kk = 0; kk < KC / 2; ++kk) {
+                        const uint64_t a = smem_desc(g0 + (uint32_t)(i * p.g_slice_bytes + kk * 256), 128, sbo);
+                        const uint64_t b = smem_desc(r0 + (uint32_t)(slot * plane_bytes + kk * 256), 128, sbo);
+                        mma_bf16(d, a, b, idesc, (j != s - 1 || kk != 0) ? 1u : 0u);
+                        issued = true;
+                    }
+                }
+                mma_commit(smem_u32(&sh->plane_empty[slot]));
+            }
+            if (!ok) break;
+            mma_commit(smem_u32(&sh->acc_full[buf]));
+        }
+        if (issued) {  // drain: every MMA this thread issued has completed before TMEM is freed
+            mma_commit(smem_u32(&sh->drain));
+            const long long t0 = clock64();
+            while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
+                if (clock64() - t0 > p.timeout_cycles) {
+                    atomicExch(p.status, FCI_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 8) tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------- helper kernels
+
+__global__ void k_absmax_bits(const double *__restrict__ x, int64_t n, unsigned long long *__restrict__ out) {
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFull);
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// C_int = round(C 2^{sh_C}), sh_C = 8 s - 3 - e_C with max|C| < 2^{e_C}: |C_int| < 2^{8s-3}
+// and |D_int| < 2^{8s-2}, inside the range of s balanced digits.
+__global__ void k_to_fixed(const double *__restrict__ C, int64_t n, int s,
+                           const unsigned long long *__restrict__ maxbits, int64_t *__restrict__ Cint,
+                           int *__restrict__ shC) {
+    const unsigned long long mb = *maxbits;
+    const int e = mb ? (int)((mb >> 52) & 0x7FF) - 1022 : 0;  // max|C| < 2^e (normal numbers)
+    const int sh = 8 * s - 3 - e;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *shC = sh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        Cint[i] = __double2ll_rn(scalbn(C[i], sh));
+}
+
+__global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, int npair,
+                                                     const int32_t *__restrict__ pairA,
+                                                     const int32_t *__restrict__ pairB,
+                                                     const int64_t *__restrict__ E, int64_t ldE,
+                                                     const double *__restrict__ C, double e_core, int ushift,
+                                                     const int *__restrict__ shC, const int *__restrict__ status,
+                                                     double *__restrict__ sigma) {
+    const int64_t ib = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (ib >= nsb) return;
+    const int u = ushift - *shC;
+    const bool bad = *status != 0;
+    for (int64_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
+        const int64_t det = ia * nsb + ib;
+        int64_t acc = 0;
+        for (int pp = 0; pp < npair; ++pp) {
+            const int64_t *Ep = E + (int64_t)pp * ldE;
+            const int32_t ea = __ldg(pairA + (int64_t)pp * nsa + ia);
+            if (ea >= 0) {
+                const int64_t e = __ldg(Ep + (int64_t)(ea >> 1) * nsb + ib);
+                acc += (ea & 1) ? -e : e;
+            }
+            const int32_t eb = __ldg(pairB + (int64_t)pp * nsb + ib);
+            if (eb >= 0) {
+                const int64_t e = __ldg(Ep + ia * nsb + (eb >> 1));
+                acc += (eb & 1) ? -e : e;
+            }
+        }
+        sigma[det] = bad ? __longlong_as_double(0x7FF8000000000000ll) : scalbn(__ll2double_rn(acc), u) + e_core * C[det];
+    }
+}
+
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int oz_kc(const fci_context *h) { return ((h->npair + 15) / 16) * 2; }
+int oz_L0(int s) { return std::max(s - 1, 2 * s - 6); }
+size_t oz_smem_bytes(int s, int KC) {
+    return 1024 + (size_t)s * 128 * KC * 16 + OZ_RING * OZ_NT * KC * 16 + sizeof(OzShared);
+}
+
+}  // namespace
+
+int oz_prepare_G(fci_context *h, int s) {
+    if (h->Gs_slices == s && h->d_Gs) return FCI_OK;
+    const int np = h->npair, KC = oz_kc(h);
+    const int Kp = KC * 8;
+    if (np > 128) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision needs <= 128 orbital pairs (n <= 15)");
+    if (s < 2 || s > OZ_MAXS) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision supports 2..%d slices", OZ_MAXS);
+    if (s * np > 1023) return fci_fail(h, FCI_ERR_UNSUPPORTED, "level sums would exceed 2^24");
+    if (oz_smem_bytes(s, KC) > 232448) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit in shared memory", s);
+    std::vector<double> G((size_t)np * np);
+    if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fci_cuda_check(h, cudaGetLastError(), "G download");
+    double gmax = 0.0;
+    for (double v : G) gmax = std::max(gmax, fabs(v));
+    int eG = 0;
+    if (gmax > 0) { frexp(gmax, &eG); }  // gmax < 2^eG
+    const int shG = 8 * s - 2 - eG;
+    uint64_t bias = 0;
+    for (int j = 0; j < s; ++j) bias |= (uint64_t)0x80 << (8 * j);
+    const size_t slice_bytes = (size_t)128 * KC * 16;
+    std::vector<uint16_t> img(slice_bytes / 2 * s, 0);
+    for (int pq = 0; pq < 128; ++pq) {
+        for (int rs = 0; rs < Kp; ++rs) {
+            int64_t gi = 0;
+            if (pq < np && rs < np) gi = llrint(ldexp(G[(size_t)pq * np + rs], shG));
+            const uint64_t y = (uint64_t)gi + bias;
+            for (int j = 0; j < s; ++j) {
+                const int d = (int)((y >> (8 * j)) & 0xFF) - 128;
+                const float f = (float)d;
+                uint32_t bits;
+                memcpy(&bits, &f, 4);
+                const size_t off = ((size_t)(pq >> 3) * KC + (rs >> 3)) * 128 + (pq & 7) * 16 + (rs & 7) * 2;
+                img[(j * slice_bytes + off) / 2] = (uint16_t)(bits >> 16);
+            }
+        }
+    }
+    fci_dev_free(h->d_Gs);
+    h->d_Gs = nullptr;
+    int rc = fci_dev_alloc(h, &h->d_Gs, img.size() * 2);
+    if (rc) return rc;
+    FCI_CUDA(h, cudaMemcpy(h->d_Gs, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
+    h->Gs_slices = s;
+    h->G_exp = shG;  // stores sh_G
+    return FCI_OK;
+}
+
+size_t oz_workspace_bytes(const fci_context *h, int s) {
+    (void)s;
+    const int64_t ldE = (h->ndet + 31) / 32 * 32;
+    return al256((size_t)h->ndet * 8) + al256((size_t)h->npair * ldE * 8) + 256;
+}
+
+int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws, size_t ws_bytes, cudaStream_t st) {
+    (void)ws_bytes;
+    if (h->mode != FCI_MODE_FCI) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision needs alpha/beta strings");
+    int rc = oz_prepare_G(h, s);
+    if (rc) return rc;
+    const int KC = oz_kc(h);
+    const int64_t N = h->ndet, ldE = (N + 31) / 32 * 32;
+    char *p = (char *)ws;
+    int64_t *Cint = (int64_t *)p;
+    p += al256((size_t)N * 8);
+    int64_t *E = (int64_t *)p;
+    p += al256((size_t)h->npair * ldE * 8);
+    unsigned long long *maxbits = (unsigned long long *)p;
+    int *shC = (int *)(p + 8);
+    int *status = (int *)(p + 16);
+    h->last_status = status;
+    {
+        phase_scope ps(h, st, FCI_PHASE_OTHER, 2);
+        FCI_CUDA(h, cudaMemsetAsync(p, 0, 256, st));
+        const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(N, 256), 152 * 8);
+        k_absmax_bits<<<nb, 256, 0, st>>>(C, N, maxbits);
+        k_to_fixed<<<nb, 256, 0, st>>>(C, N, s, maxbits, Cint, shC);
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    OzParams prm;
+    prm.N = N;
+    prm.nsa = h->nsa;
+    prm.nsb = h->nsb;
+    prm.npair = h->npair;
+    prm.KC = KC;
+    prm.s = s;
+    prm.L0 = oz_L0(s);
+    prm.g_slice_bytes = 128 * KC * 16;
+    prm.pairA = h->d_pair_a;
+    prm.pairB = h->d_pair_b;
+    prm.Cint = Cint;
+    prm.Gimg = (const uint4 *)h->d_Gs;
+    prm.E = E;
+    prm.ldE = ldE;
+    prm.status = status;
+    const char *to = getenv("FCI_WAIT_TIMEOUT_MS");
+    const double ms = to ? atof(to) : 2000.0;
+    prm.timeout_cycles = (long long)(ms * 2.1e6);  // cycles at up to 2.1 GHz
+    const char *stall = getenv("FCI_TEST_STALL_PRODUCER");
+    prm.stall_test = stall ? atoi(stall) : 0;
+    const size_t smem = oz_smem_bytes(s, KC);
+    FCI_CUDA(h, cudaFuncSetAttribute(k_oz_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nsm = 0;
+    FCI_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const int64_t ntiles = (N + OZ_NT - 1) / OZ_NT;
+    const unsigned grid = (unsigned)std::min<int64_t>(nsm, ntiles);
+    {
+        phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
+        k_oz_contract<<<grid, OZ_THREADS, smem, st>>>(prm);
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    {
+        phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
+        const int threads = 128;
+        dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
+        k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, h->d_pair_a, h->d_pair_b, E, ldE, C,
+                                           h->e_core, 8 * prm.L0 - h->G_exp, shC, status, sigma);
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    return FCI_OK;
 }

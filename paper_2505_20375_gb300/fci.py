@@ -46,7 +46,7 @@ class fci_info(ctypes.Structure):
 class fci_davidson_opts(ctypes.Structure):
     _fields_ = [("max_iter", _i32), ("max_subspace", _i32), ("tol_residual", _dbl), ("tol_energy", _dbl),
                 ("eps", _dbl), ("precision", _i32), ("n_slices", _i32), ("switch_residual", _dbl),
-                ("use_guess", _i32)]
+                ("use_guess", _i32), ("final_precision", _i32), ("final_slices", _i32)]
 
 
 class fci_davidson_iter(ctypes.Structure):
@@ -85,6 +85,7 @@ _tbytes = _sig("fci_table_bytes", [_vp, _i32, ctypes.POINTER(_sz)])
 _tcopy = _sig("fci_copy_table", [_vp, _i32, _vp, _sz, _vp])
 _set_timing = _sig("fci_set_phase_timing", [_vp, _i32])
 _get_times = _sig("fci_get_phase_times", [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), _i32])
+_sync_status = _sig("fci_sync_status", [_vp, _vp])
 PHASES = ("gather", "contract", "scatter", "other")
 
 
@@ -238,13 +239,14 @@ class FCI:
 
     def davidson(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                  precision="fp64", n_slices=6, switch_residual=1e-5, guess: torch.Tensor = None,
-                 stream=None) -> DavidsonResult:
+                 final_precision="fp64", final_slices=0, stream=None) -> DavidsonResult:
         o = fci_davidson_opts()
         _dav_defaults(ctypes.byref(o))
         o.max_iter, o.max_subspace = max_iter, max_subspace
         o.tol_residual, o.tol_energy, o.eps = tol_residual, tol_energy, eps
         o.precision, o.n_slices, o.switch_residual = PRECISIONS[precision], n_slices, switch_residual
         o.use_guess = 1 if guess is not None else 0
+        o.final_precision, o.final_slices = PRECISIONS[final_precision], final_slices
         b = _sz()
         self._check(_dav_ws(self._h, ctypes.byref(o), ctypes.byref(b)))
         p, nb = self._workspace(b.value)
@@ -260,6 +262,10 @@ class FCI:
             self._check(rc)
         its = [{k: getattr(iters[i], k) for k, _ in fci_davidson_iter._fields_} for i in range(log.n_iter)]
         return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its)
+
+    def sync_status(self, stream=None):
+        """Synchronise and raise FCIError(FCI_ERR_TIMEOUT) if a device wait expired."""
+        self._check(_sync_status(self._h, _stream(stream)))
 
     # ------------------------------------------------------------- timing
     def set_phase_timing(self, enable: bool = True):
