@@ -49,7 +49,7 @@ struct fci_das_layout {
     std::vector<int64_t> cat_off;           // offsets in the intermediate space order
     int64_t n_det = 0, n_det_int = 0;
     // device arrays
-    int64_t *d_cat_of_pair = nullptr;       // [n_pat_a * n_pat_b] -> offset or -1 (intermediate addr)
+    int32_t *d_cat_of_pair = nullptr;       // [n_pat_a * n_pat_b] -> category index or -1
     int32_t *d_loc_a = nullptr;             // [n_str_a]: local index of each global alpha string
     int32_t *d_pat_of_a = nullptr;          // [n_str_a]: pattern id (or -1 if excess > T+1)
     int32_t *d_loc_b = nullptr, *d_pat_of_b = nullptr;

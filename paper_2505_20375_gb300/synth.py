@@ -150,7 +150,9 @@ def hubbard_dimer(t: float, U: float):
 WORKLOADS = {
     "fci_8e8o": dict(n=8, na=4, nb=4, n_chol=16, seed=1),
     "fci_14e14o": dict(n=14, na=7, nb=7, n_chol=28, seed=2),
+    "fci_12e12o": dict(n=12, na=6, nb=6, n_chol=24, seed=2),
     "das_24o_4x6": dict(n=24, spaces=[6, 6, 6, 6], ref=[3, 3, 3, 3], max_transfer=2, n_chol=48, seed=3),
     "das_16o_4x4": dict(n=16, spaces=[4, 4, 4, 4], ref=[2, 2, 2, 2], max_transfer=2, n_chol=48, seed=3),
+    "das_16o_4x4_8e": dict(n=16, spaces=[4, 4, 4, 4], ref=[1, 1, 1, 1], max_transfer=1, n_chol=48, seed=5),
     "spinor_24s12e": dict(n=24, ne=12, n_chol=48, seed=4),
 }

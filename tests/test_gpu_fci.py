@@ -205,9 +205,10 @@ def test_argument_errors_are_codes_not_faults(fci_lib):
     from paper_2505_20375_gb300 import fci
 
     f = fci.FCI(0)
-    with pytest.raises(fci.FCIError) as e:
-        f.sigma(torch.zeros(4, dtype=torch.float64, device="cuda"))
-    assert e.value.code == fci.FCI_ERR_STATE
+    z = torch.zeros(4, dtype=torch.float64, device="cuda")
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    rc = fci._sigma(f._h, z.data_ptr(), z.data_ptr() + 0, 1, 0, 0, ws.data_ptr(), 1024, None)
+    assert rc == fci.FCI_ERR_STATE  # sigma before any strings
     h, g = synth.real_integrals(4, 2, 1)
     g_bad = g.copy()
     g_bad[0, 1, 2, 3] += 1e-3
