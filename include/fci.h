@@ -251,6 +251,28 @@ int fci_set_phase_timing(fci_handle h, int enable);
  * (launches[FCI_N_PHASES]); either pointer may be NULL.  reset != 0 clears the sums. */
 int fci_get_phase_times(fci_handle h, double *ms, int64_t *launches, int reset);
 
+/* ------------------------------------------------------- allocation-free sigma */
+
+/* sigma = H C for ONE vector in FP64, like fci_sigma with precision FCI_PREC_FP64, but
+ * with its scratch (the D and E intermediates, 2 x n_pair x n_det elements) in a
+ * fixed 64 MiB device array inside libfci instead of a caller workspace.  The paper
+ * has no counterpart; this exists for callers that cannot allocate device memory when
+ * they need sigma: a process whose framework already reserved the device memory pool,
+ * code running where CUDA allocation calls are not allowed (e.g. a host callback on a
+ * stream), or a latency-critical loop that must avoid the implicit synchronisation of
+ * cudaMalloc/cudaFree.  It calls no allocating routine.
+ *   C, sigma: DEVICE pointers, info.n_det elements each (double or interleaved complex),
+ *             not overlapping; FCI and spinor layouts (not DAS).
+ *   Sizes whose scratch exceeds 64 MiB are rejected with FCI_ERR_ARG (use fci_sigma).
+ * The array is a device variable: every GPU that loads libfci holds it until exit.  The
+ * first call on each device looks up its address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture.  All calls share
+ * the one array and it keeps the last call's contents (every byte a call reads it
+ * writes first); calls that overlap on the GPU (other streams, other threads, other
+ * handles on the same device) race on it and must be serialised by the caller.
+ * Asynchronous on `stream`. */
+int fci_sigma_noalloc(fci_handle h, const void *C, void *sigma, fci_stream stream);
+
 #ifdef __cplusplus
 }
 #endif
