@@ -4,8 +4,10 @@
 // Both operands go to fixed point with one exponent each (C and hence D by
 // 2^{sh_C}, G by 2^{sh_G}) and are cut into s signed base-256 digits in [-128, 127]:
 //   X_int = sum_{j<s} x_j 256^j.
-// Digits are exact in bf16, products of two digits are below 2^14, and every partial
-// sum of the MMA stays an integer below 2^24, so the FP32 accumulation in TMEM is exact.
+// Digits are exact in f16 (the tensor rate of f16 and bf16 is the same; f16 makes the
+// digit-to-float conversion two integer instructions and one packed subtraction per two
+// digits), products of two digits are below 2^14, and every partial sum of the MMA stays
+// an integer below 2^24, so the FP32 accumulation in TMEM is exact.
 // The product is regrouped by significance level L = i + j of the digit pair; only the
 // top s levels (L >= s - 1) are formed (the usual triangular truncation), each into its
 // own TMEM accumulator:
@@ -16,13 +18,13 @@
 //   sigma_I = 2^{8 L0 - sh_G - sh_C} sum <I|E_pq|K> E_int[pq, K] + e_core C_I.
 // (Methods, Eqs. sigmaL/sigmaL2e: E = g' D is the dense contraction of the sigma build.)
 //
-// Kernel layout (one persistent CTA per SM, 288 threads):
-//   warps 0-3  producers: gather D_int for a tile of 32 determinants from the fixed-point
+// Kernel layout (one persistent CTA per SM, 544 threads):
+//   warps 0-7  producers: gather D_int for a tile of 32 determinants from the fixed-point
 //              C and the pair tables, keep it in registers, and write its s digit planes
-//              (bf16, canonical K-major core-matrix layout) into a 3-slot shared ring;
-//   warps 4-7  epilogue: read the s level accumulators of a tile from TMEM (one warp per
-//              32-lane quadrant), combine them in int64, store E_int rows;
-//   warp 8     allocates TMEM; lane 0 issues tcgen05.mma (M = 128 pair rows of G digits
+//              (f16, canonical K-major core-matrix layout) into a 3-slot shared ring;
+//   warps 8-15 epilogue: read the s level accumulators of a tile from TMEM (two warps per
+//              32-lane quadrant, 16 columns each), combine them in int64, store E_int rows;
+//   warp 16    allocates TMEM; lane 0 issues tcgen05.mma (M = 128 pair rows of G digits
 //              resident in shared memory, N = 32 determinants, K = 16 per instruction) and
 //              tcgen05.commit to the mbarriers that hand buffers between the roles.
 // Level accumulators are double-buffered (2 x s x 32 TMEM columns).  Every wait on an
@@ -34,11 +36,16 @@
 
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "fci_internal.h"
 
 namespace {
 
-constexpr int OZ_THREADS = 288;
+constexpr int OZ_PRODUCER_WARPS = 8;
+constexpr int OZ_EPILOGUE_WARPS = 8;  // two per TMEM lane quadrant, 16 columns each
+constexpr int OZ_MMA_WARP = OZ_PRODUCER_WARPS + OZ_EPILOGUE_WARPS;
+constexpr int OZ_THREADS = 32 * (OZ_MMA_WARP + 1);  // 544
 constexpr int OZ_NT = 32;   // determinants per tile (MMA N)
 constexpr int OZ_RING = 3;  // digit-plane slots
 constexpr int OZ_MAXS = 7;
@@ -82,8 +89,8 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
-// D[tmem] (+)= A[smem] * B[smem]^T, bf16 inputs, fp32 accumulate.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+// D[tmem] (+)= A[smem] * B[smem]^T, 16-bit float inputs, fp32 accumulate.
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -96,17 +103,13 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-// 32 consecutive 32-bit TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive 32-bit TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -119,16 +122,19 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor, kind::f16: D f32, A and B f16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-// bf16 bits of the integer d in [-128, 127] (exact): 2^23 + 2^22 + d in fp32, minus
-// the offset, keeps all 8 significant bits in the upper half of the fp32 word.
-__device__ __forceinline__ uint32_t digit_f32(uint32_t byte) {
-    const float f = __uint_as_float(0x4B3FFF80u + byte) - 12582912.0f;
-    return __float_as_uint(f);
+// Two balanced base-256 digits as an f16x2 word, exactly: the bytes b0, b1 of the
+// biased value land in the low bits of two halves whose exponent field is that of 1024
+// (0x6400 | b encodes 1024 + b exactly), and one packed subtraction of 1024 + 128
+// leaves b - 128 in [-128, 127].
+__device__ __forceinline__ uint32_t digits_f16x2(uint32_t x, uint32_t y, uint32_t sel) {
+    const uint32_t w = (__byte_perm(x, y, sel) & 0x00FF00FFu) | 0x64006400u;
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&w), __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)));
+    return *reinterpret_cast<const uint32_t *>(&h);
 }
 
 struct OzParams {
@@ -200,18 +206,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
     }
     if (threadIdx.x == 0) {
         for (int r = 0; r < OZ_RING; ++r) {
-            mbar_init(smem_u32(&sh->plane_full[r]), 4);
+            mbar_init(smem_u32(&sh->plane_full[r]), OZ_PRODUCER_WARPS);
             mbar_init(smem_u32(&sh->plane_empty[r]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&sh->acc_full[b]), 1);
-            mbar_init(smem_u32(&sh->acc_empty[b]), 4);
+            mbar_init(smem_u32(&sh->acc_empty[b]), OZ_EPILOGUE_WARPS);
         }
         mbar_init(smem_u32(&sh->drain), 1);
         sh->abort = 0;
         fence_barrier_init();
     }
-    if (warp == 8) {
+    if (warp == OZ_MMA_WARP) {
         tmem_alloc(smem_u32(&sh->tmem_base), 512);
         tmem_relinquish();
     }
@@ -223,20 +229,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
     volatile int *abort = &sh->abort;
     const int64_t ntiles = (p.N + OZ_NT - 1) / OZ_NT;
 
-    if (warp < 4) {
+    if (warp < OZ_PRODUCER_WARPS) {
         // ---------------------------------------------------------------- producers
-        const int t = threadIdx.x;  // 0..127
+        const int t = threadIdx.x;  // 0..255
         const int units = OZ_NT * KC;
+        constexpr int PT = 32 * OZ_PRODUCER_WARPS;
+        uint64_t bias = 0;
+        for (int j = 0; j < s; ++j) bias |= (uint64_t)0x80 << (8 * j);
         uint32_t q = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            int64_t dint[4][8];
+            // biased fixed-point D: Y = D_int + sum_j 128 256^j, kept as two 32-bit halves
+            uint32_t ylo[2][8], yhi[2][8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int unit = t + 128 * u;
+            for (int u = 0; u < 2; ++u) {
+                const int unit = t + PT * u;
                 const int r = unit % OZ_NT, c = unit / OZ_NT;
                 const int64_t det = tile * OZ_NT + r;
+                int64_t dv[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) dint[u][e] = 0;
+                for (int e = 0; e < 8; ++e) dv[e] = 0;
                 if (unit < units && det < p.N) {
                     const int64_t ka = det / p.nsb, kb = det - ka * p.nsb;
                     const int64_t *Crow = p.Cint + ka * p.nsb;
@@ -244,25 +255,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
                     for (int e = 0; e < 8; ++e) {
                         const int rs = 8 * c + e;
                         if (rs < p.npair) {
-                            int64_t v = 0;
                             const int32_t ea = __ldg(p.pairA + (int64_t)rs * p.nsa + ka);
+                            const int32_t eb = __ldg(p.pairB + (int64_t)rs * p.nsb + kb);
+                            int64_t v = 0;
                             if (ea >= 0) {
                                 const int64_t x = __ldg(p.Cint + (int64_t)(ea >> 1) * p.nsb + kb);
                                 v = (ea & 1) ? -x : x;
                             }
-                            const int32_t eb = __ldg(p.pairB + (int64_t)rs * p.nsb + kb);
                             if (eb >= 0) {
                                 const int64_t x = __ldg(Crow + (eb >> 1));
                                 v += (eb & 1) ? -x : x;
                             }
-                            dint[u][e] = v;
+                            dv[e] = v;
                         }
                     }
                 }
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const uint64_t y = (uint64_t)dv[e] + bias;
+                    ylo[u][e] = (uint32_t)y;
+                    yhi[u][e] = (uint32_t)(y >> 32);
+                }
             }
-            // biased digits: Y = D_int + sum_j 128 256^j, digit_j = byte_j(Y) - 128
-            uint64_t bias = 0;
-            for (int j = 0; j < s; ++j) bias |= (uint64_t)0x80 << (8 * j);
             for (int j = s - 1; j >= 0; --j, ++q) {
                 const int slot = q % OZ_RING;
                 const uint32_t use = q / OZ_RING;
@@ -270,19 +284,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
                                              p.timeout_cycles))
                     goto producer_done;
                 uint8_t *plane = sRing + slot * plane_bytes;
+                const uint32_t bj = (uint32_t)(j & 3);
+                const uint32_t sel = bj | ((4u + bj) << 8);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int unit = t + 128 * u;
+                for (int u = 0; u < 2; ++u) {
+                    const int unit = t + PT * u;
                     if (unit >= units) continue;
                     const int r = unit % OZ_NT, c = unit / OZ_NT;
                     uint32_t w[4];
 #pragma unroll
-                    for (int e = 0; e < 8; e += 2) {
-                        const uint64_t y0 = (uint64_t)dint[u][e] + bias, y1 = (uint64_t)dint[u][e + 1] + bias;
-                        const uint32_t f0 = digit_f32((uint32_t)(y0 >> (8 * j)) & 0xFFu);
-                        const uint32_t f1 = digit_f32((uint32_t)(y1 >> (8 * j)) & 0xFFu);
-                        w[e / 2] = __byte_perm(f0, f1, 0x7632);
-                    }
+                    for (int e = 0; e < 8; e += 2)
+                        w[e / 2] = j < 4 ? digits_f16x2(ylo[u][e], ylo[u][e + 1], sel)
+                                         : digits_f16x2(yhi[u][e], yhi[u][e + 1], sel);
                     const uint32_t off = (uint32_t)(((r >> 3) * KC + c) * 128 + (r & 7) * 16);
                     *(uint4 *)(plane + off) = make_uint4(w[0], w[1], w[2], w[3]);
                 }
@@ -292,9 +305,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
             }
         }
     producer_done:;
-    } else if (warp < 8) {
+    } else if (warp < OZ_MMA_WARP) {
         // ---------------------------------------------------------------- epilogue
-        const int qd = warp - 4;  // TMEM lane quadrant: rows 32 qd .. 32 qd + 31
+        const int ew = warp - OZ_PRODUCER_WARPS;
+        const int qd = ew & 3;          // TMEM lane quadrant: rows 32 qd .. 32 qd + 31
+        const int c0 = 16 * (ew >> 2);  // this warp's 16 of the tile's 32 columns
         const int row = 32 * qd + lane;
         const int lowshift = 8 * (p.L0 - (s - 1));
         uint32_t tau = 0;
@@ -303,28 +318,28 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
             if (!oz_wait_warp(smem_u32(&sh->acc_full[buf]), (tau >> 1) & 1, abort, p.status, p.timeout_cycles))
                 break;
             tc_fence_after();
-            int64_t acc[OZ_NT];
+            int64_t acc[16];
 #pragma unroll
-            for (int c = 0; c < OZ_NT; ++c) acc[c] = 0;
+            for (int c = 0; c < 16; ++c) acc[c] = 0;
             for (int L = s - 1; L <= 2 * s - 2; ++L) {
-                uint32_t v[32];
-                const uint32_t col = (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT);
-                tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + col, v);
+                uint32_t v[16];
+                const uint32_t col = (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT + c0);
+                tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + col, v);
                 tmem_ld_wait();
                 if (L < p.L0) {
                     const int sh8 = 8 * (L - (s - 1));
 #pragma unroll
-                    for (int c = 0; c < OZ_NT; ++c)
+                    for (int c = 0; c < 16; ++c)
                         acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << sh8);
                 } else {
                     if (L == p.L0 && lowshift > 0) {
                         const int64_t half = (int64_t)1 << (lowshift - 1);
 #pragma unroll
-                        for (int c = 0; c < OZ_NT; ++c) acc[c] = (acc[c] + half) >> lowshift;
+                        for (int c = 0; c < 16; ++c) acc[c] = (acc[c] + half) >> lowshift;
                     }
                     const int sh8 = 8 * (L - p.L0);
 #pragma unroll
-                    for (int c = 0; c < OZ_NT; ++c)
+                    for (int c = 0; c < 16; ++c)
                         acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << sh8);
                 }
             }
@@ -332,21 +347,21 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
             if (row < p.npair) {
-                const int64_t d0 = tile * OZ_NT;
+                const int64_t d0 = tile * OZ_NT + c0;
                 int64_t *dst = p.E + (int64_t)row * p.ldE + d0;
-                if (d0 + OZ_NT <= p.N) {
+                if (d0 + 16 <= p.N) {
 #pragma unroll
-                    for (int c = 0; c < OZ_NT; c += 2)
+                    for (int c = 0; c < 16; c += 2)
                         *(longlong2 *)(dst + c) = make_longlong2(acc[c], acc[c + 1]);
                 } else {
-                    for (int c = 0; c < OZ_NT; ++c)
+                    for (int c = 0; c < 16; ++c)
                         if (d0 + c < p.N) dst[c] = acc[c];
                 }
             }
         }
     } else if (lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
-        const uint32_t idesc = idesc_bf16(128, OZ_NT);
+        const uint32_t idesc = idesc_f16(128, OZ_NT);
         const uint32_t sbo = (uint32_t)(KC * 128);
         const uint32_t g0 = smem_u32(sG), r0 = smem_u32(sRing);
         uint32_t q = 0, tau = 0;
@@ -366,13 +381,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
                     break;
                 }
                 tc_fence_after();
-                for (int i = s - 1 - j; i < s; ++i) {
-                    const int L = i + j;
-                    const uint32_t d = tmem + (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT);
-                    for (int kk = 0; kk < KC / 2; ++kk) {
+                // consecutive MMAs go to different level accumulators (no back-to-back
+                // dependency on one accumulator while another level can proceed)
+                for (int kk = 0; kk < KC / 2; ++kk) {
+                    const uint64_t b = smem_desc(r0 + (uint32_t)(slot * plane_bytes + kk * 256), 128, sbo);
+                    for (int i = s - 1 - j; i < s; ++i) {
+                        const int L = i + j;
+                        const uint32_t d = tmem + (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT);
                         const uint64_t a = smem_desc(g0 + (uint32_t)(i * p.g_slice_bytes + kk * 256), 128, sbo);
-                        const uint64_t b = smem_desc(r0 + (uint32_t)(slot * plane_bytes + kk * 256), 128, sbo);
-                        mma_bf16(d, a, b, idesc, (j != s - 1 || kk != 0) ? 1u : 0u);
+                        mma_f16(d, a, b, idesc, (j != s - 1 || kk != 0) ? 1u : 0u);
                         issued = true;
                     }
                 }
@@ -395,7 +412,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 8) tmem_dealloc(tmem, 512);
+    if (warp == OZ_MMA_WARP) tmem_dealloc(tmem, 512);
 }
 
 // ------------------------------------------------------------- helper kernels
@@ -462,6 +479,16 @@ size_t oz_smem_bytes(int s, int KC) {
 
 }  // namespace
 
+// IEEE binary16 encoding of an integer |d| <= 1024 (exact).
+static uint16_t half_bits_of_small_int(int d) {
+    if (d == 0) return 0;
+    const uint16_t sign = d < 0 ? 0x8000 : 0;
+    unsigned m = (unsigned)(d < 0 ? -d : d);
+    int e = 31 - __builtin_clz(m);  // m in [2^e, 2^(e+1))
+    const unsigned mant = (m << (10 - e)) & 0x3FF;
+    return (uint16_t)(sign | ((unsigned)(e + 15) << 10) | mant);
+}
+
 int oz_prepare_G(fci_context *h, int s) {
     if (h->Gs_slices == s && h->d_Gs) return FCI_OK;
     const int np = h->npair, KC = oz_kc(h);
@@ -489,11 +516,8 @@ int oz_prepare_G(fci_context *h, int s) {
             const uint64_t y = (uint64_t)gi + bias;
             for (int j = 0; j < s; ++j) {
                 const int d = (int)((y >> (8 * j)) & 0xFF) - 128;
-                const float f = (float)d;
-                uint32_t bits;
-                memcpy(&bits, &f, 4);
                 const size_t off = ((size_t)(pq >> 3) * KC + (rs >> 3)) * 128 + (pq & 7) * 16 + (rs & 7) * 2;
-                img[(j * slice_bytes + off) / 2] = (uint16_t)(bits >> 16);
+                img[(j * slice_bytes + off) / 2] = half_bits_of_small_int(d);
             }
         }
     }
