@@ -396,11 +396,12 @@ int fci_build_strings(fci_handle h, int n_alpha, int n_beta, fci_stream stream) 
         FCI_CUDA(h, launch_strings_unrank(n, n_beta, nsb, h->d_binom, h->d_str_b, s));
         rc = fci_dev_alloc(h, (void **)&h->d_rep_a, (size_t)nsa * h->nent_a * 8);
         if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_rep_b, (size_t)nsb * h->nent_b * 8);
-        if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_pair_a, (size_t)nsa * h->npair * 4);
-        if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_pair_b, (size_t)nsb * h->npair * 4);
+        h->npair_pad = (h->npair + 15) / 16 * 16;
+        if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_pair_a, (size_t)nsa * h->npair_pad * 4);
+        if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_pair_b, (size_t)nsb * h->npair_pad * 4);
         if (rc) { free_strings(h); return rc; }
-        FCI_CUDA(h, launch_repl_table(n, n_alpha, nsa, h->d_str_a, h->d_binom, h->nent_a, 1, h->d_rep_a, h->d_pair_a, h->npair, s));
-        FCI_CUDA(h, launch_repl_table(n, n_beta, nsb, h->d_str_b, h->d_binom, h->nent_b, 1, h->d_rep_b, h->d_pair_b, h->npair, s));
+        FCI_CUDA(h, launch_repl_table(n, n_alpha, nsa, h->d_str_a, h->d_binom, h->nent_a, 1, h->d_rep_a, h->d_pair_a, h->npair_pad, s));
+        FCI_CUDA(h, launch_repl_table(n, n_beta, nsb, h->d_str_b, h->d_binom, h->nent_b, 1, h->d_rep_b, h->d_pair_b, h->npair_pad, s));
         h->mode = FCI_MODE_FCI;
     } else {
         // The list of every spinor string is kept only when it is small; the sigma kernels

@@ -77,6 +77,7 @@ struct fci_context {
     int64_t nsa = 0, nsb = 0, ndet = 0;
     int nent_a = 0, nent_b = 0;
     int npair = 0;
+    int npair_pad = 0;  // rows of the dense pair tables: n_pair rounded up to 16 (extra rows = -1)
 
     uint64_t *d_binom = nullptr;   // [65*65]
     uint64_t *d_str_a = nullptr, *d_str_b = nullptr;

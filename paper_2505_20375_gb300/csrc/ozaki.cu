@@ -188,19 +188,21 @@ __device__ __forceinline__ bool oz_wait_warp(uint32_t bar, uint32_t parity, vola
     return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
 }
 
+template <int S>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-    const int s = p.s, KC = p.KC;
+    const int KC = p.KC;
     const int plane_bytes = OZ_NT * KC * 16;
     uint8_t *sG = smem;
-    uint8_t *sRing = sG + (size_t)s * p.g_slice_bytes;
+    uint8_t *sRing = sG + (size_t)S * p.g_slice_bytes;
     OzShared *sh = (OzShared *)(sRing + OZ_RING * plane_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int L0 = (S - 1 > 2 * S - 6) ? S - 1 : 2 * S - 6;
 
     // G digit slices: one copy per CTA, reused for every tile
     {
-        const int n16 = s * p.g_slice_bytes / 16;
+        const int n16 = S * p.g_slice_bytes / 16;
         uint4 *dst = (uint4 *)sG;
         for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(p.Gimg + i);
     }
@@ -231,53 +233,44 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
 
     if (warp < OZ_PRODUCER_WARPS) {
         // ---------------------------------------------------------------- producers
+        // Thread t owns units (det r, K-core c) t and t + 256 of the tile: 8 pair
+        // indices rs = 8c..8c+7 of one determinant.  The pair tables have rows up to the
+        // padded K, filled with -1, so no range test is needed.
         const int t = threadIdx.x;  // 0..255
         const int units = OZ_NT * KC;
         constexpr int PT = 32 * OZ_PRODUCER_WARPS;
-        uint64_t bias = 0;
-        for (int j = 0; j < s; ++j) bias |= (uint64_t)0x80 << (8 * j);
+        constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
         uint32_t q = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            // biased fixed-point D: Y = D_int + sum_j 128 256^j, kept as two 32-bit halves
             uint32_t ylo[2][8], yhi[2][8];
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
                 const int unit = t + PT * u;
                 const int r = unit % OZ_NT, c = unit / OZ_NT;
                 const int64_t det = tile * OZ_NT + r;
-                int64_t dv[8];
+                const bool live = unit < units && det < p.N;
+                const int64_t ka = live ? det / p.nsb : 0, kb = live ? det - ka * p.nsb : 0;
+                const int64_t *Crow = p.Cint + ka * p.nsb;
+                int32_t ea[8], eb[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) dv[e] = 0;
-                if (unit < units && det < p.N) {
-                    const int64_t ka = det / p.nsb, kb = det - ka * p.nsb;
-                    const int64_t *Crow = p.Cint + ka * p.nsb;
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int rs = 8 * c + e;
-                        if (rs < p.npair) {
-                            const int32_t ea = __ldg(p.pairA + (int64_t)rs * p.nsa + ka);
-                            const int32_t eb = __ldg(p.pairB + (int64_t)rs * p.nsb + kb);
-                            int64_t v = 0;
-                            if (ea >= 0) {
-                                const int64_t x = __ldg(p.Cint + (int64_t)(ea >> 1) * p.nsb + kb);
-                                v = (ea & 1) ? -x : x;
-                            }
-                            if (eb >= 0) {
-                                const int64_t x = __ldg(Crow + (eb >> 1));
-                                v += (eb & 1) ? -x : x;
-                            }
-                            dv[e] = v;
-                        }
-                    }
+                for (int e = 0; e < 8; ++e) {
+                    const int rs = 8 * c + e;
+                    ea[e] = live ? __ldg(p.pairA + (int64_t)rs * p.nsa + ka) : -1;
+                    eb[e] = live ? __ldg(p.pairB + (int64_t)rs * p.nsb + kb) : -1;
                 }
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const uint64_t y = (uint64_t)dv[e] + bias;
+                    const int64_t xa = __ldg(p.Cint + (int64_t)(ea[e] >= 0 ? (ea[e] >> 1) : 0) * p.nsb + kb);
+                    const int64_t xb = __ldg(Crow + (eb[e] >= 0 ? (eb[e] >> 1) : 0));
+                    int64_t v = ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa : xa);
+                    v += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb : xb);
+                    const uint64_t y = (uint64_t)v + bias;
                     ylo[u][e] = (uint32_t)y;
                     yhi[u][e] = (uint32_t)(y >> 32);
                 }
             }
-            for (int j = s - 1; j >= 0; --j, ++q) {
+#pragma unroll
+            for (int j = S - 1; j >= 0; --j, ++q) {
                 const int slot = q % OZ_RING;
                 const uint32_t use = q / OZ_RING;
                 if (use > 0 && !oz_wait_warp(smem_u32(&sh->plane_empty[slot]), (use - 1) & 1, abort, p.status,
@@ -311,36 +304,35 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
         const int qd = ew & 3;          // TMEM lane quadrant: rows 32 qd .. 32 qd + 31
         const int c0 = 16 * (ew >> 2);  // this warp's 16 of the tile's 32 columns
         const int row = 32 * qd + lane;
-        const int lowshift = 8 * (p.L0 - (s - 1));
+        constexpr int lowshift = 8 * (L0 - (S - 1));
         uint32_t tau = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
             const int buf = tau & 1;
             if (!oz_wait_warp(smem_u32(&sh->acc_full[buf]), (tau >> 1) & 1, abort, p.status, p.timeout_cycles))
                 break;
             tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * OZ_NT + c0);
             int64_t acc[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[c] = 0;
-            for (int L = s - 1; L <= 2 * s - 2; ++L) {
+#pragma unroll
+            for (int L = S - 1; L <= 2 * S - 2; ++L) {
                 uint32_t v[16];
-                const uint32_t col = (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT + c0);
-                tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + col, v);
+                tmem_ld16(tbase + (uint32_t)((L - (S - 1)) * OZ_NT), v);
                 tmem_ld_wait();
-                if (L < p.L0) {
-                    const int sh8 = 8 * (L - (s - 1));
+                if (L < L0) {
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
-                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << sh8);
+                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * (L - (S - 1))));
                 } else {
-                    if (L == p.L0 && lowshift > 0) {
-                        const int64_t half = (int64_t)1 << (lowshift - 1);
+                    if (L == L0 && lowshift > 0) {
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) acc[c] = (acc[c] + half) >> lowshift;
+                        for (int c = 0; c < 16; ++c)
+                            acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
                     }
-                    const int sh8 = 8 * (L - p.L0);
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
-                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << sh8);
+                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * (L - L0)));
                 }
             }
             tc_fence_before();
@@ -361,9 +353,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
         }
     } else if (lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
+        // Descriptors differ only in the 14-bit start-address field: one base per G slice
+        // and per ring slot, plus 16 (= 256 bytes >> 4) per K-step.
         const uint32_t idesc = idesc_f16(128, OZ_NT);
         const uint32_t sbo = (uint32_t)(KC * 128);
-        const uint32_t g0 = smem_u32(sG), r0 = smem_u32(sRing);
+        uint64_t adesc[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i) adesc[i] = smem_desc(smem_u32(sG) + (uint32_t)(i * p.g_slice_bytes), 128, sbo);
+        const uint64_t bdesc0 = smem_desc(smem_u32(sRing), 128, sbo);
+        const uint32_t bstep = (uint32_t)(plane_bytes >> 4);  // ring slots are contiguous
+        const int ksteps = KC / 2;
         uint32_t q = 0, tau = 0;
         bool issued = false;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
@@ -372,8 +371,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
                                      p.timeout_cycles))
                 break;
             tc_fence_after();
+            const uint32_t dbase = tmem + (uint32_t)(buf * S * OZ_NT);
             bool ok = true;
-            for (int j = s - 1; j >= 0; --j, ++q) {
+#pragma unroll
+            for (int j = S - 1; j >= 0; --j, ++q) {
                 const int slot = q % OZ_RING;
                 if (!oz_wait(smem_u32(&sh->plane_full[slot]), (q / OZ_RING) & 1, abort, p.status,
                              p.timeout_cycles)) {
@@ -381,18 +382,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
                     break;
                 }
                 tc_fence_after();
-                // consecutive MMAs go to different level accumulators (no back-to-back
-                // dependency on one accumulator while another level can proceed)
-                for (int kk = 0; kk < KC / 2; ++kk) {
-                    const uint64_t b = smem_desc(r0 + (uint32_t)(slot * plane_bytes + kk * 256), 128, sbo);
-                    for (int i = s - 1 - j; i < s; ++i) {
-                        const int L = i + j;
-                        const uint32_t d = tmem + (uint32_t)(buf * s * OZ_NT + (L - (s - 1)) * OZ_NT);
-                        const uint64_t a = smem_desc(g0 + (uint32_t)(i * p.g_slice_bytes + kk * 256), 128, sbo);
-                        mma_f16(d, a, b, idesc, (j != s - 1 || kk != 0) ? 1u : 0u);
-                        issued = true;
-                    }
+                const uint64_t b0 = bdesc0 + (uint64_t)(slot * bstep);
+                for (int kk = 0; kk < ksteps; ++kk) {
+                    const uint64_t b = b0 + (uint64_t)(kk * 16);
+                    const uint32_t acc_in = (j != S - 1 || kk != 0) ? 1u : 0u;
+#pragma unroll
+                    for (int i = S - 1 - j; i < S; ++i)
+                        mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * OZ_NT), adesc[i] + (uint64_t)(kk * 16), b,
+                                idesc, acc_in);
                 }
+                issued = true;
                 mma_commit(smem_u32(&sh->plane_empty[slot]));
             }
             if (!ok) break;
@@ -583,14 +582,24 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
     const char *stall = getenv("FCI_TEST_STALL_PRODUCER");
     prm.stall_test = stall ? atoi(stall) : 0;
     const size_t smem = oz_smem_bytes(s, KC);
-    FCI_CUDA(h, cudaFuncSetAttribute(k_oz_contract, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void (*kern)(OzParams) = nullptr;
+    switch (s) {
+        case 2: kern = k_oz_contract<2>; break;
+        case 3: kern = k_oz_contract<3>; break;
+        case 4: kern = k_oz_contract<4>; break;
+        case 5: kern = k_oz_contract<5>; break;
+        case 6: kern = k_oz_contract<6>; break;
+        case 7: kern = k_oz_contract<7>; break;
+        default: return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d", s);
+    }
+    FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nsm = 0;
     FCI_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     const int64_t ntiles = (N + OZ_NT - 1) / OZ_NT;
     const unsigned grid = (unsigned)std::min<int64_t>(nsm, ntiles);
     {
         phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
-        k_oz_contract<<<grid, OZ_THREADS, smem, st>>>(prm);
+        kern<<<grid, OZ_THREADS, smem, st>>>(prm);
         FCI_CUDA(h, cudaGetLastError());
     }
     {
