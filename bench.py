@@ -158,7 +158,6 @@ def run_ours(a, rank, world, local_rank):
 
     ref = sigma("fp64", 0).clone()
     torch.cuda.synchronize()
-    oz_ok = False
     for s_try in range(2, 8):
         try:
             oz = sigma("oz_bf16", s_try).clone()
@@ -172,12 +171,15 @@ def run_ours(a, rank, world, local_rank):
             e1.synchronize()
             variants[f"oz_bf16_s{s_try}"] = {"rel_err_vs_fp64": err, "ms": e0.elapsed_time(e1) / 3,
                                              "det_sigma_per_s": N / (e0.elapsed_time(e1) / 3e3)}
-            if s_try == slices:
-                oz_ok = err <= 1e-11
         except fci.FCIError as e:
             variants[f"oz_bf16_s{s_try}"] = {"unavailable": str(e)[:200]}
+    # FP64-class split: the fastest slice count whose sigma meets the 1e-11 parity bar
+    passing = [(v["ms"], int(k.rsplit("s", 1)[1])) for k, v in variants.items()
+               if "ms" in v and v["rel_err_vs_fp64"] <= 1e-11]
     if prec == "best":
-        prec = "oz_bf16" if oz_ok else "fp64"
+        prec = "oz_bf16" if passing else "fp64"
+        if passing:
+            slices = min(passing)[1]
     n_sl = slices if prec == "oz_bf16" else 0
 
     # FP64 peak of this GPU, measured in this run (cuBLAS DGEMM through torch)
@@ -286,13 +288,15 @@ def run_ours(a, rank, world, local_rank):
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops_sustained": 1700.0}
-        pad_m, pad_k = 128, 112
+        pad_m, pad_k = 128, (npair + 15) // 16 * 16
         bf16_flops = 2.0 * pad_m * pad_k * N * (n_sl * (n_sl + 1) // 2)
         achieved = bf16_flops / (ms_launch * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "kernel": "k_oz_contract (tcgen05 bf16)", "achieved": achieved, "peak": peak,
+        roof = {"bound": "tensor", "kernel": "k_oz_contract (tcgen05.mma kind::f16, fp16 digit slices)",
+                "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; f16 and bf16 share the rate)",
+                "flops_counted": "executed MMA work: 2 x 128 (pair rows, padded) x K_pad x N x s(s+1)/2"}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

@@ -46,8 +46,11 @@ constexpr int OZ_PRODUCER_WARPS = 8;
 constexpr int OZ_EPILOGUE_WARPS = 8;  // two per TMEM lane quadrant, 16 columns each
 constexpr int OZ_MMA_WARP = OZ_PRODUCER_WARPS + OZ_EPILOGUE_WARPS;
 constexpr int OZ_THREADS = 32 * (OZ_MMA_WARP + 1);  // 544
-constexpr int OZ_NT = 32;   // determinants per tile (MMA N)
-constexpr int OZ_RING = 3;  // digit-plane slots
+constexpr int OZ_MAX_RING = 3;  // digit-plane slots (2 or 3, whatever shared memory allows)
+// Determinants per tile (the MMA's N).  A tcgen05.mma costs at least ~45 cycles to issue
+// whatever its size, so an M=128 N=32 K=16 MMA reaches only about a third of the tensor
+// rate; N=64 is the largest tile for which the s level accumulators fit in TMEM (s <= 7).
+constexpr int OZ_TILE = 64;
 constexpr int OZ_MAXS = 7;
 
 // ------------------------------------------------------------------ PTX helpers
@@ -148,6 +151,7 @@ struct OzParams {
     int *status;
     long long timeout_cycles;
     int stall_test;
+    int ring;  // digit-plane slots in use
 };
 
 // Warp-uniform variant: lane 0 waits, every lane gets the same answer, so no lane can
@@ -156,7 +160,7 @@ __device__ __forceinline__ bool oz_wait_warp(uint32_t bar, uint32_t parity, vola
                                              long long timeout);
 
 struct OzShared {  // lives after the operand buffers
-    uint64_t plane_full[OZ_RING], plane_empty[OZ_RING];
+    uint64_t plane_full[OZ_MAX_RING], plane_empty[OZ_MAX_RING];
     uint64_t acc_full[2], acc_empty[2];
     uint64_t drain;
     uint32_t tmem_base;
@@ -188,17 +192,22 @@ __device__ __forceinline__ bool oz_wait_warp(uint32_t bar, uint32_t parity, vola
     return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
 }
 
-template <int S>
+// S: slices per operand; NT: determinants per tile (the MMA's N).  Accumulators are
+// double-buffered when 2 x S x NT TMEM columns fit in 512, single-buffered otherwise.
+template <int S, int NT>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
+    constexpr int NBUF = (2 * S * NT <= 512) ? 2 : 1;
+    constexpr int PT = 32 * OZ_PRODUCER_WARPS;
+    constexpr int UNITS = (NT * 16 + PT - 1) / PT;  // producer units per thread (KC <= 16)
+    constexpr int L0 = (S - 1 > 2 * S - 6) ? S - 1 : 2 * S - 6;
     extern __shared__ __align__(1024) uint8_t oz_smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)oz_smem_raw + 1023) & ~(uintptr_t)1023);
-    const int KC = p.KC;
-    const int plane_bytes = OZ_NT * KC * 16;
+    const int KC = p.KC, RING = p.ring;
+    const int plane_bytes = NT * KC * 16;
     uint8_t *sG = smem;
     uint8_t *sRing = sG + (size_t)S * p.g_slice_bytes;
-    OzShared *sh = (OzShared *)(sRing + OZ_RING * plane_bytes);
+    OzShared *sh = (OzShared *)(sRing + RING * plane_bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int L0 = (S - 1 > 2 * S - 6) ? S - 1 : 2 * S - 6;
 
     // G digit slices: one copy per CTA, reused for every tile
     {
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
         for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(p.Gimg + i);
     }
     if (threadIdx.x == 0) {
-        for (int r = 0; r < OZ_RING; ++r) {
+        for (int r = 0; r < RING; ++r) {
             mbar_init(smem_u32(&sh->plane_full[r]), OZ_PRODUCER_WARPS);
             mbar_init(smem_u32(&sh->plane_empty[r]), 1);
         }
@@ -229,28 +238,32 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
     tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
     volatile int *abort = &sh->abort;
-    const int64_t ntiles = (p.N + OZ_NT - 1) / OZ_NT;
+    // Each CTA takes one contiguous range of tiles, so consecutive tiles of a CTA share
+    // alpha strings and read the same rows of C (cache and TLB locality).
+    const int64_t ntiles = (p.N + NT - 1) / NT;
+    const int64_t t_begin = ntiles * blockIdx.x / gridDim.x, t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
 
     if (warp < OZ_PRODUCER_WARPS) {
         // ---------------------------------------------------------------- producers
-        // Thread t owns units (det r, K-core c) t and t + 256 of the tile: 8 pair
+        // Thread t owns units (det r, K-core c) t, t + 256, ... of the tile: 8 pair
         // indices rs = 8c..8c+7 of one determinant.  The pair tables have rows up to the
         // padded K, filled with -1, so no range test is needed.
         const int t = threadIdx.x;  // 0..255
-        const int units = OZ_NT * KC;
-        constexpr int PT = 32 * OZ_PRODUCER_WARPS;
+        const int units = NT * KC;
         constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
         uint32_t q = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            uint32_t ylo[2][8], yhi[2][8];
+        for (int64_t tile = t_begin; tile < t_end; ++tile) {
+            uint32_t ylo[UNITS][8], yhi[UNITS][8];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < UNITS; ++u) {
                 const int unit = t + PT * u;
-                const int r = unit % OZ_NT, c = unit / OZ_NT;
-                const int64_t det = tile * OZ_NT + r;
-                const bool live = unit < units && det < p.N;
-                const int64_t ka = live ? det / p.nsb : 0, kb = live ? det - ka * p.nsb : 0;
-                const int64_t *Crow = p.Cint + ka * p.nsb;
+                const int r = unit % NT, c = unit / NT;
+                // determinant counts of the split path fit 32 bits (n <= 15 orbitals)
+                const uint32_t det = (uint32_t)tile * NT + (uint32_t)r;
+                const bool live = unit < units && det < (uint32_t)p.N;
+                const uint32_t nsb = (uint32_t)p.nsb;
+                const uint32_t ka = live ? det / nsb : 0u, kb = live ? det - ka * nsb : 0u;
+                const int64_t *Crow = p.Cint + (int64_t)ka * nsb;
                 int32_t ea[8], eb[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
@@ -271,8 +284,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
             }
 #pragma unroll
             for (int j = S - 1; j >= 0; --j, ++q) {
-                const int slot = q % OZ_RING;
-                const uint32_t use = q / OZ_RING;
+                const int slot = q % RING;
+                const uint32_t use = q / RING;
                 if (use > 0 && !oz_wait_warp(smem_u32(&sh->plane_empty[slot]), (use - 1) & 1, abort, p.status,
                                              p.timeout_cycles))
                     goto producer_done;
@@ -280,10 +293,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
                 const uint32_t bj = (uint32_t)(j & 3);
                 const uint32_t sel = bj | ((4u + bj) << 8);
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
+                for (int u = 0; u < UNITS; ++u) {
                     const int unit = t + PT * u;
                     if (unit >= units) continue;
-                    const int r = unit % OZ_NT, c = unit / OZ_NT;
+                    const int r = unit % NT, c = unit / NT;
                     uint32_t w[4];
 #pragma unroll
                     for (int e = 0; e < 8; e += 2)
@@ -300,62 +313,69 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
     producer_done:;
     } else if (warp < OZ_MMA_WARP) {
         // ---------------------------------------------------------------- epilogue
+        // Warp (quadrant qd, half h) reads lanes 32 qd .. 32 qd + 31 and columns
+        // [h NT/2, (h+1) NT/2) in chunks of 16, every level of a chunk into int64.
         const int ew = warp - OZ_PRODUCER_WARPS;
-        const int qd = ew & 3;          // TMEM lane quadrant: rows 32 qd .. 32 qd + 31
-        const int c0 = 16 * (ew >> 2);  // this warp's 16 of the tile's 32 columns
+        const int qd = ew & 3;
+        const int cbeg = (NT / 2) * (ew >> 2);
         const int row = 32 * qd + lane;
         constexpr int lowshift = 8 * (L0 - (S - 1));
         uint32_t tau = 0;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
-            const int buf = tau & 1;
-            if (!oz_wait_warp(smem_u32(&sh->acc_full[buf]), (tau >> 1) & 1, abort, p.status, p.timeout_cycles))
-                break;
+        for (int64_t tile = t_begin; tile < t_end; ++tile, ++tau) {
+            const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
+            const uint32_t par = NBUF == 2 ? (tau >> 1) & 1 : tau & 1;
+            if (!oz_wait_warp(smem_u32(&sh->acc_full[buf]), par, abort, p.status, p.timeout_cycles)) break;
             tc_fence_after();
-            const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * OZ_NT + c0);
-            int64_t acc[16];
+            const uint32_t tlane = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * NT);
+            int64_t *dst_tile = p.E + tile * ((int64_t)p.npair * NT) + (int64_t)row * NT;
+#pragma unroll 1
+            for (int c0 = cbeg; c0 < cbeg + NT / 2; c0 += 16) {
+                int64_t acc[16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[c] = 0;
+                for (int c = 0; c < 16; ++c) acc[c] = 0;
 #pragma unroll
-            for (int L = S - 1; L <= 2 * S - 2; ++L) {
-                uint32_t v[16];
-                tmem_ld16(tbase + (uint32_t)((L - (S - 1)) * OZ_NT), v);
-                tmem_ld_wait();
-                if (L < L0) {
-#pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * (L - (S - 1))));
-                } else {
-                    if (L == L0 && lowshift > 0) {
+                for (int L = S - 1; L <= 2 * S - 2; ++L) {
+                    uint32_t v[16];
+                    tmem_ld16(tlane + (uint32_t)((L - (S - 1)) * NT + c0), v);
+                    tmem_ld_wait();
+                    if (L < L0) {
 #pragma unroll
                         for (int c = 0; c < 16; ++c)
-                            acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
-                    }
+                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * (L - (S - 1))));
+                    } else {
+                        if (L == L0 && lowshift > 0) {
 #pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * (L - L0)));
+                            for (int c = 0; c < 16; ++c)
+                                acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * (L - L0)));
+                    }
+                }
+                if (row < p.npair) {
+                    // tile-major E: the block of one tile (n_pair rows x NT) is contiguous
+                    const int64_t d0 = tile * NT + c0;
+                    int64_t *dst = dst_tile + c0;
+                    if (d0 + 16 <= p.N) {
+#pragma unroll
+                        for (int c = 0; c < 16; c += 2)  // streaming stores: E is read once, by the scatter
+                            __stcs((longlong2 *)(dst + c), make_longlong2(acc[c], acc[c + 1]));
+                    } else {
+                        for (int c = 0; c < 16; ++c)
+                            if (d0 + c < p.N) dst[c] = acc[c];
+                    }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
-            if (row < p.npair) {
-                const int64_t d0 = tile * OZ_NT + c0;
-                int64_t *dst = p.E + (int64_t)row * p.ldE + d0;
-                if (d0 + 16 <= p.N) {
-#pragma unroll
-                    for (int c = 0; c < 16; c += 2)
-                        *(longlong2 *)(dst + c) = make_longlong2(acc[c], acc[c + 1]);
-                } else {
-                    for (int c = 0; c < 16; ++c)
-                        if (d0 + c < p.N) dst[c] = acc[c];
-                }
-            }
         }
     } else if (lane == 0) {
         // ---------------------------------------------------------------- MMA issuer
         // Descriptors differ only in the 14-bit start-address field: one base per G slice
-        // and per ring slot, plus 16 (= 256 bytes >> 4) per K-step.
-        const uint32_t idesc = idesc_f16(128, OZ_NT);
+        // and for the ring, plus 16 (= 256 bytes >> 4) per K-step.
+        const uint32_t idesc = idesc_f16(128, NT);
         const uint32_t sbo = (uint32_t)(KC * 128);
         uint64_t adesc[S];
 #pragma unroll
@@ -365,18 +385,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
         const int ksteps = KC / 2;
         uint32_t q = 0, tau = 0;
         bool issued = false;
-        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tau) {
-            const int buf = tau & 1;
-            if (tau >= 2 && !oz_wait(smem_u32(&sh->acc_empty[buf]), ((tau >> 1) - 1) & 1, abort, p.status,
-                                     p.timeout_cycles))
-                break;
+        for (int64_t tile = t_begin; tile < t_end; ++tile, ++tau) {
+            const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
+            if (tau >= (uint32_t)NBUF) {
+                const uint32_t par = NBUF == 2 ? ((tau >> 1) - 1) & 1 : (tau - 1) & 1;
+                if (!oz_wait(smem_u32(&sh->acc_empty[buf]), par, abort, p.status, p.timeout_cycles)) break;
+            }
             tc_fence_after();
-            const uint32_t dbase = tmem + (uint32_t)(buf * S * OZ_NT);
+            const uint32_t dbase = tmem + (uint32_t)(buf * S * NT);
             bool ok = true;
 #pragma unroll
             for (int j = S - 1; j >= 0; --j, ++q) {
-                const int slot = q % OZ_RING;
-                if (!oz_wait(smem_u32(&sh->plane_full[slot]), (q / OZ_RING) & 1, abort, p.status,
+                const int slot = q % RING;
+                if (!oz_wait(smem_u32(&sh->plane_full[slot]), (q / RING) & 1, abort, p.status,
                              p.timeout_cycles)) {
                     ok = false;
                     break;
@@ -388,7 +409,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
                     const uint32_t acc_in = (j != S - 1 || kk != 0) ? 1u : 0u;
 #pragma unroll
                     for (int i = S - 1 - j; i < S; ++i)
-                        mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * OZ_NT), adesc[i] + (uint64_t)(kk * 16), b,
+                        mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * NT), adesc[i] + (uint64_t)(kk * 16), b,
                                 idesc, acc_in);
                 }
                 issued = true;
@@ -448,19 +469,22 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
     if (ib >= nsb) return;
     const int u = ushift - *shC;
     const bool bad = *status != 0;
+    // E is tile-major: element (pq, K) at (K / T) * n_pair * T + pq * T + K % T, T = OZ_TILE
+    const int64_t tstride = (int64_t)npair * OZ_TILE;
     for (int64_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
         const int64_t det = ia * nsb + ib;
         int64_t acc = 0;
         for (int pp = 0; pp < npair; ++pp) {
-            const int64_t *Ep = E + (int64_t)pp * ldE;
             const int32_t ea = __ldg(pairA + (int64_t)pp * nsa + ia);
             if (ea >= 0) {
-                const int64_t e = __ldg(Ep + (int64_t)(ea >> 1) * nsb + ib);
+                const int64_t K = (int64_t)(ea >> 1) * nsb + ib;
+                const int64_t e = __ldg(E + (K / OZ_TILE) * tstride + pp * OZ_TILE + (K % OZ_TILE));
                 acc += (ea & 1) ? -e : e;
             }
             const int32_t eb = __ldg(pairB + (int64_t)pp * nsb + ib);
             if (eb >= 0) {
-                const int64_t e = __ldg(Ep + ia * nsb + (eb >> 1));
+                const int64_t K = ia * nsb + (eb >> 1);
+                const int64_t e = __ldg(E + (K / OZ_TILE) * tstride + pp * OZ_TILE + (K % OZ_TILE));
                 acc += (eb & 1) ? -e : e;
             }
         }
@@ -472,8 +496,14 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int oz_kc(const fci_context *h) { return ((h->npair + 15) / 16) * 2; }
 int oz_L0(int s) { return std::max(s - 1, 2 * s - 6); }
-size_t oz_smem_bytes(int s, int KC) {
-    return 1024 + (size_t)s * 128 * KC * 16 + OZ_RING * OZ_NT * KC * 16 + sizeof(OzShared);
+constexpr size_t OZ_SMEM_MAX = 232448;
+size_t oz_smem_bytes(int s, int KC, int ring) {
+    return 1024 + (size_t)s * 128 * KC * 16 + (size_t)ring * OZ_TILE * KC * 16 + sizeof(OzShared);
+}
+int oz_ring(int s, int KC) {
+    if (oz_smem_bytes(s, KC, 3) <= OZ_SMEM_MAX) return 3;
+    if (oz_smem_bytes(s, KC, 2) <= OZ_SMEM_MAX) return 2;
+    return 0;
 }
 
 }  // namespace
@@ -493,9 +523,10 @@ int oz_prepare_G(fci_context *h, int s) {
     const int np = h->npair, KC = oz_kc(h);
     const int Kp = KC * 8;
     if (np > 128) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision needs <= 128 orbital pairs (n <= 15)");
+    if (h->ndet >= ((int64_t)1 << 31)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision needs < 2^31 determinants");
     if (s < 2 || s > OZ_MAXS) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision supports 2..%d slices", OZ_MAXS);
     if (s * np > 1023) return fci_fail(h, FCI_ERR_UNSUPPORTED, "level sums would exceed 2^24");
-    if (oz_smem_bytes(s, KC) > 232448) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit in shared memory", s);
+    if (!oz_ring(s, KC)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit in shared memory", s);
     std::vector<double> G((size_t)np * np);
     if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fci_cuda_check(h, cudaGetLastError(), "G download");
@@ -532,8 +563,8 @@ int oz_prepare_G(fci_context *h, int s) {
 
 size_t oz_workspace_bytes(const fci_context *h, int s) {
     (void)s;
-    const int64_t ldE = (h->ndet + 31) / 32 * 32;
-    return al256((size_t)h->ndet * 8) + al256((size_t)h->npair * ldE * 8) + 256;
+    const int64_t ntiles = (h->ndet + OZ_TILE - 1) / OZ_TILE;
+    return al256((size_t)h->ndet * 8) + al256((size_t)ntiles * h->npair * OZ_TILE * 8) + 256;
 }
 
 int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws, size_t ws_bytes, cudaStream_t st) {
@@ -547,7 +578,7 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
     int64_t *Cint = (int64_t *)p;
     p += al256((size_t)N * 8);
     int64_t *E = (int64_t *)p;
-    p += al256((size_t)h->npair * ldE * 8);
+    p += al256((size_t)((N + OZ_TILE - 1) / OZ_TILE) * h->npair * OZ_TILE * 8);
     unsigned long long *maxbits = (unsigned long long *)p;
     int *shC = (int *)(p + 8);
     int *status = (int *)(p + 16);
@@ -581,21 +612,22 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
     prm.timeout_cycles = (long long)(ms * 2.1e6);  // cycles at up to 2.1 GHz
     const char *stall = getenv("FCI_TEST_STALL_PRODUCER");
     prm.stall_test = stall ? atoi(stall) : 0;
-    const size_t smem = oz_smem_bytes(s, KC);
+    prm.ring = oz_ring(s, KC);
+    const size_t smem = oz_smem_bytes(s, KC, prm.ring);
     void (*kern)(OzParams) = nullptr;
     switch (s) {
-        case 2: kern = k_oz_contract<2>; break;
-        case 3: kern = k_oz_contract<3>; break;
-        case 4: kern = k_oz_contract<4>; break;
-        case 5: kern = k_oz_contract<5>; break;
-        case 6: kern = k_oz_contract<6>; break;
-        case 7: kern = k_oz_contract<7>; break;
+        case 2: kern = k_oz_contract<2, OZ_TILE>; break;
+        case 3: kern = k_oz_contract<3, OZ_TILE>; break;
+        case 4: kern = k_oz_contract<4, OZ_TILE>; break;
+        case 5: kern = k_oz_contract<5, OZ_TILE>; break;
+        case 6: kern = k_oz_contract<6, OZ_TILE>; break;
+        case 7: kern = k_oz_contract<7, OZ_TILE>; break;
         default: return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d", s);
     }
     FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int nsm = 0;
     FCI_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const int64_t ntiles = (N + OZ_NT - 1) / OZ_NT;
+    const int64_t ntiles = (N + OZ_TILE - 1) / OZ_TILE;
     const unsigned grid = (unsigned)std::min<int64_t>(nsm, ntiles);
     {
         phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
