@@ -213,6 +213,58 @@ int davidson_solve(fci_handle h, const fci_davidson_opts *opts, void *C_io, doub
                    fci_davidson_log *log, void *workspace, size_t workspace_bytes,
                    fci_stream stream);
 
+/* fci_sigma for one vector, replayed from a CUDA graph: the first call with a given
+ * (C, sigma, precision, n_slices, workspace, stream) runs the sigma once, then captures
+ * its kernel sequence into a graph kept in the handle (at most 64 graphs; the oldest is
+ * dropped); later calls with the same arguments launch the graph.  Must not be called
+ * while `stream` is itself being captured.  Results equal fci_sigma's. */
+int fci_sigma_graph(fci_handle h, const void *C, void *sigma, int precision, int n_slices, void *workspace,
+                    size_t workspace_bytes, fci_stream stream);
+/* Drop the handle's cached sigma graphs (e.g. before freeing the buffers they name). */
+int fci_clear_graphs(fci_handle h);
+
+/* ------------------------------------------------- grouped sigma, step-wise Davidson */
+
+/* One sigma build of a batch: sigma = H C for one vector of the problem held by handle. */
+typedef struct {
+    fci_handle handle;
+    const void *C;          /* DEVICE, info.n_det elements */
+    void *sigma;            /* DEVICE, info.n_det elements */
+    int precision;          /* FCI_PREC_* */
+    int n_slices;
+    void *workspace;        /* DEVICE, >= fci_sigma_workspace_bytes of the job's handle */
+    size_t workspace_bytes;
+} fci_sigma_job;
+
+/* sigma builds of several problems (different handles, sizes and integrals) in one pass
+ * on `stream`: jobs that use FCI_PREC_OZ_BF16 on alpha/beta strings with the same slice
+ * count share ONE persistent launch of the tcgen05 contraction kernel (the uneven tile
+ * ranges of all jobs in one grid, CTAs split in proportion to each job's tiles); the other
+ * jobs run one after another.  All handles must be on the same device; a handle may
+ * appear in at most one job.  Asynchronous.  This is the batching the serving loop uses
+ * for the sigma builds of concurrent Davidson solves (not a step of the paper's method). */
+int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream);
+
+typedef struct fci_davidson_state *fci_davidson_handle;
+
+/* Davidson driven by the caller's sigma products (same iteration as davidson_solve):
+ *   davidson_begin  sets up the solve (diagonal, start vector C_guess or the unit vector
+ *                   at min H_II) and requests the first product;
+ *   davidson_request returns the pending request: y (DEVICE) must receive H x, with the
+ *                   precision and slice count this iteration uses, and the part of the
+ *                   Davidson workspace reserved for the sigma build;
+ *   davidson_advance consumes y = H x, updates the subspace and either sets *done or
+ *                   leaves a new request;
+ *   davidson_finish  copies the Ritz vector to C_out (DEVICE, may be NULL), returns the
+ *                   energy and log, and frees the state (also after an error).
+ * One solve at a time per handle (the handle's small scratch holds the projected matrix). */
+int davidson_begin(fci_handle h, const fci_davidson_opts *opts, const void *C_guess, void *workspace,
+                   size_t workspace_bytes, fci_stream stream, fci_davidson_handle *out);
+int davidson_request(fci_davidson_handle st, const void **x, void **y, int *precision, int *n_slices,
+                     void **sigma_workspace, size_t *sigma_workspace_bytes);
+int davidson_advance(fci_davidson_handle st, int *done);
+int davidson_finish(fci_davidson_handle st, void *C_out, double *energy, fci_davidson_log *log);
+
 /* ------------------------------------------------------------ table export */
 
 enum {

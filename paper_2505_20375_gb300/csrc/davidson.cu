@@ -12,6 +12,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <new>
+#include <vector>
 
 #include "fci_internal.h"
 
@@ -366,13 +368,302 @@ __global__ void k_set_unit(double *__restrict__ x, int64_t nreal, int cplx, cons
 
 inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
-struct dav_ws {
-    double *V, *S, *c, *sc, *cp, *scp, *t, *diag;
-    void *sig_ws;
-    size_t sig_bytes;
-};
-
 }  // namespace
+
+// Davidson as a state machine: run_until_sigma() advances the iteration until the next
+// sigma product is needed (it then exposes x and y = H x to the caller) or until the
+// solve ends.  davidson_solve drives it with the library's own sigma; the step-wise C ABI
+// (davidson_begin/advance/finish) lets a scheduler compute the sigma products of many
+// solves together.
+struct fci_davidson_state {
+    enum { REQ_NONE = 0, REQ_INIT, REQ_SWITCH, REQ_APPEND };
+    fci_context *h = nullptr;
+    fci_davidson_opts o{};
+    cudaStream_t s = nullptr;
+    int64_t n = 0, nreal = 0, ldv = 0;
+    bool cplx = false;
+    size_t esz = 8, vec = 0;
+    int ms = 0;
+    double *V = nullptr, *S = nullptr, *c = nullptr, *sc = nullptr, *cp = nullptr, *scp = nullptr, *t = nullptr,
+           *diag = nullptr;
+    void *sig_ws = nullptr;
+    size_t sig_bytes = 0;
+    double *partial = nullptr, *Hs = nullptr, *dots = nullptr, *y = nullptr, *nrm = nullptr;
+    dav_scalars *scal = nullptr;
+    int64_t *argmin = nullptr;
+    unsigned vb = 1;
+    // iteration state
+    int k = 0, it = 0, it_rec = 0, phase1_iters = 0, n_sigma = 0;
+    int prec = FCI_PREC_FP64, slices = 0;
+    bool final_phase = true, have_prev = false, converged = false, done = false;
+    double E_prev = 0.0, lam_pending = 0.0;
+    int request = REQ_NONE;
+    double *req_x = nullptr, *req_y = nullptr;
+    std::chrono::steady_clock::time_point t_iter;
+    std::vector<fci_davidson_iter> log;
+    int status = FCI_OK;
+
+    double *Vk(int i) { return (double *)((char *)V + (size_t)i * vec); }
+    double *Sk(int i) { return (double *)((char *)S + (size_t)i * vec); }
+
+    cudaError_t multidot(const double *Vb, int kk, const double *x, double *out) {
+        if (cplx) k_multidot<true><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, kk, x, n, partial);
+        else k_multidot<false><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, kk, x, n, partial);
+        k_reduce_partial<<<1, 64, 0, s>>>(partial, vb, kk, out);
+        return cudaGetLastError();
+    }
+    cudaError_t lincomb(const double *Vb, int kk, const double *yy, double scale, double *out, int acc) {
+        if (cplx) k_lincomb<true><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, kk, yy, scale, n, out, acc);
+        else k_lincomb<false><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, kk, yy, scale, n, out, acc);
+        return cudaGetLastError();
+    }
+    cudaError_t normalize(double *x, double *n2out) {
+        k_norm2<<<vb, RED_THREADS, 0, s>>>(x, nreal, partial);
+        k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, n2out);
+        k_scale<<<vb, RED_THREADS, 0, s>>>(x, nreal, n2out);
+        return cudaGetLastError();
+    }
+    // New subspace column kk: Hs[:, kk] = V^H S_kk.
+    int add_column(int kk) {
+        FCI_CUDA(h, multidot(V, kk + 1, Sk(kk), dots));
+        k_hsub_update<<<1, 64, 0, s>>>(Hs, dots, kk);
+        FCI_CUDA(h, cudaGetLastError());
+        return FCI_OK;
+    }
+    void ask(int kind, double *x, double *yv) {
+        request = kind;
+        req_x = x;
+        req_y = yv;
+        ++n_sigma;
+    }
+
+    int init(fci_context *hh, const fci_davidson_opts *oo, const void *guess, void *ws, cudaStream_t st) {
+        h = hh;
+        o = *oo;
+        s = st;
+        n = h->das_active ? h->das.n_det : h->ndet;
+        cplx = h->dtype == FCI_C128;
+        esz = cplx ? 16 : 8;
+        nreal = cplx ? 2 * n : n;
+        vec = al((size_t)n * esz);
+        ms = o.max_subspace;
+        char *p = (char *)ws;
+        V = (double *)p; p += ms * vec;
+        S = (double *)p; p += ms * vec;
+        c = (double *)p; p += vec;
+        sc = (double *)p; p += vec;
+        cp = (double *)p; p += vec;
+        scp = (double *)p; p += vec;
+        t = (double *)p; p += vec;
+        diag = (double *)p; p += al((size_t)n * 8);
+        sig_ws = p;
+        size_t sig = sigma_ws_bytes(h, o.precision, o.n_slices);
+        if (o.precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, o.final_precision, o.final_slices));
+        sig_bytes = al(sig);
+        ldv = (int64_t)(vec / esz);
+        double *small = h->d_small;
+        partial = small;                           // RED_BLOCKS * 2 * KMAX
+        Hs = partial + RED_BLOCKS * 2 * KMAX;      // 2 * KMAX * KMAX
+        dots = Hs + 2 * KMAX * KMAX;               // 2 * KMAX
+        y = dots + 2 * KMAX;                       // 2 * KMAX
+        nrm = y + 2 * KMAX;                        // 4
+        scal = (dav_scalars *)(nrm + 4);
+        argmin = (int64_t *)(scal + 1);
+        vb = (unsigned)std::min<int64_t>(RED_BLOCKS, std::max<int64_t>(1, ceil_div(n, RED_THREADS)));
+        prec = o.precision;
+        slices = o.n_slices;
+        final_phase = o.precision == FCI_PREC_FP64 || (o.precision == o.final_precision && o.n_slices == o.final_slices);
+        FCI_CUDA(h, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         2 * (2 * KMAX) * (2 * KMAX + 1) * (int)sizeof(double)));
+        if (h->das_active) FCI_CUDA(h, launch_diag_das(h, diag, s));
+        else if (h->mode == FCI_MODE_SPINOR) FCI_CUDA(h, launch_diag_spinor(h, diag, s));
+        else FCI_CUDA(h, launch_diag_fci(h, diag, s));
+        if (guess) {
+            FCI_CUDA(h, cudaMemcpyAsync(Vk(0), guess, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+        } else {
+            k_argmin<<<1, 256, 0, s>>>(diag, n, argmin);
+            k_set_unit<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, cplx, argmin);
+        }
+        FCI_CUDA(h, normalize(Vk(0), nrm));
+        ask(REQ_INIT, Vk(0), Sk(0));
+        return FCI_OK;
+    }
+
+    // The caller has written y = H x for the pending request.
+    int consume_sigma() {
+        int rc;
+        switch (request) {
+            case REQ_INIT:
+                FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
+                if ((rc = add_column(0))) return rc;
+                k = 1;
+                break;
+            case REQ_SWITCH:
+                FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
+                if ((rc = add_column(0))) return rc;
+                k = 1;
+                FCI_CUDA(h, cudaMemcpyAsync(cp, c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                have_prev = true;
+                E_prev = lam_pending;
+                break;
+            case REQ_APPEND:
+                if ((rc = add_column(k))) return rc;
+                ++k;
+                break;
+            default:
+                return fci_fail(h, FCI_ERR_STATE, "no sigma product was requested");
+        }
+        request = REQ_NONE;
+        return FCI_OK;
+    }
+
+    // Advance until the next sigma request (returns FCI_OK with request != REQ_NONE) or
+    // until the solve ends (done = true).
+    int run_until_sigma() {
+        int rc;
+        dav_scalars hs{};
+        while (!done) {
+            if (it >= o.max_iter) {
+                done = true;
+                break;
+            }
+            ++it;
+            t_iter = std::chrono::steady_clock::now();
+            {
+                const int m = cplx ? 2 * k : k;
+                k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, y, scal);
+            }
+            FCI_CUDA(h, lincomb(V, k, y, 1.0, c, 0));
+            FCI_CUDA(h, lincomb(S, k, y, 1.0, sc, 0));
+            if (have_prev) {
+                FCI_CUDA(h, multidot(cp, 1, c, dots));  // <c_prev|c>
+                FCI_CUDA(h, cudaMemcpyAsync(&scal->ov_re, dots, 16, cudaMemcpyDeviceToDevice, s));
+            }
+            if (cplx) k_residual<true><<<vb, RED_THREADS, 0, s>>>(c, sc, cp, have_prev, diag, scal, n, t, partial);
+            else k_residual<false><<<vb, RED_THREADS, 0, s>>>(c, sc, cp, have_prev, diag, scal, n, t, partial);
+            k_reduce_residual<<<1, 32, 0, s>>>(partial, vb, scal);
+            FCI_CUDA(h, cudaGetLastError());
+            FCI_CUDA(h, cudaMemcpyAsync(&hs, scal, sizeof hs, cudaMemcpyDeviceToHost, s));
+            FCI_CUDA(h, cudaStreamSynchronize(s));
+            const double lam = hs.lam, rn = sqrt(hs.rnorm2);
+            const double dE = it > 1 ? lam - E_prev : 0.0;
+            const auto t1 = std::chrono::steady_clock::now();
+            fci_davidson_iter r;
+            r.iteration = it;
+            r.precision = prec;
+            r.energy = lam;  // sigma carries e_core C
+            r.delta_energy = dE;
+            r.max_delta_c = have_prev ? hs.maxdc : 0.0;
+            r.residual_norm = rn;
+            r.seconds = std::chrono::duration<double>(t1 - t_iter).count();
+            log.push_back(r);
+            if (!isfinite(lam) || !isfinite(rn)) return fci_fail(h, FCI_ERR_CUDA, "Davidson produced a non-finite value");
+            if (!final_phase) {
+                ++phase1_iters;
+                if (rn <= o.switch_residual || phase1_iters >= o.max_iter / 2) {
+                    // Residual correction: restart from the Ritz vector with the final precision.
+                    final_phase = true;
+                    prec = o.final_precision;
+                    slices = o.final_slices;
+                    FCI_CUDA(h, cudaMemcpyAsync(Vk(0), c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                    FCI_CUDA(h, normalize(Vk(0), nrm));
+                    lam_pending = lam;
+                    ask(REQ_SWITCH, Vk(0), Sk(0));
+                    return FCI_OK;
+                }
+            } else if (rn <= o.tol_residual && it > 1 && fabs(dE) <= o.tol_energy) {
+                converged = true;
+                E_prev = lam;
+                done = true;
+                break;
+            }
+            if (o.eps > 0.0) {
+                if (cplx) k_threshold<true><<<vb, RED_THREADS, 0, s>>>(t, n, scal, o.eps);
+                else k_threshold<false><<<vb, RED_THREADS, 0, s>>>(t, n, scal, o.eps);
+            }
+            if (k >= ms) {
+                // collapse to the current and previous Ritz vectors (sigma by linearity)
+                // V_0 = c / ||c||, S_0 = sc / ||c||
+                FCI_CUDA(h, cudaMemcpyAsync(Vk(0), c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                FCI_CUDA(h, cudaMemcpyAsync(Sk(0), sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, partial);
+                k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+                k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, nrm);
+                k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(0), nreal, nrm);
+                int knew = 1;
+                if (have_prev && ms > 2) {
+                    // p = c_prev - <c|c_prev> c, S_p = sc_prev - <c|c_prev> sc, both / ||p||.
+                    // Two Gram-Schmidt passes: c and c_prev are nearly parallel near
+                    // convergence, and one pass leaves an orthogonality error of eps / ||p||
+                    // that compounds over successive collapses.
+                    FCI_CUDA(h, cudaMemcpyAsync(Vk(1), cp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                    FCI_CUDA(h, cudaMemcpyAsync(Sk(1), scp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                    for (int pass = 0; pass < 2; ++pass) {
+                        FCI_CUDA(h, multidot(Vk(0), 1, Vk(1), dots));
+                        k_negate<<<1, 64, 0, s>>>(dots, 1);
+                        FCI_CUDA(h, lincomb(Vk(0), 1, dots, 1.0, Vk(1), 1));
+                        FCI_CUDA(h, lincomb(Sk(0), 1, dots, 1.0, Sk(1), 1));
+                    }
+                    k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, partial);
+                    k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+                    double pn2 = 0.0;
+                    FCI_CUDA(h, cudaMemcpyAsync(&pn2, nrm, 8, cudaMemcpyDeviceToHost, s));
+                    FCI_CUDA(h, cudaStreamSynchronize(s));
+                    if (sqrt(pn2) > 1e-10) {
+                        k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, nrm);
+                        k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(1), nreal, nrm);
+                        knew = 2;
+                    }
+                }
+                FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
+                for (int jj = 0; jj < knew; ++jj)
+                    if ((rc = add_column(jj))) return rc;
+                k = knew;
+            }
+            // two rounds of classical Gram-Schmidt against V[0..k)
+            for (int round = 0; round < 2; ++round) {
+                FCI_CUDA(h, multidot(V, k, t, dots));
+                k_negate<<<1, 64, 0, s>>>(dots, k);
+                FCI_CUDA(h, lincomb(V, k, dots, 1.0, t, 1));
+            }
+            k_norm2<<<vb, RED_THREADS, 0, s>>>(t, nreal, partial);
+            k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+            double tn2 = 0.0;
+            FCI_CUDA(h, cudaMemcpyAsync(&tn2, nrm, 8, cudaMemcpyDeviceToHost, s));
+            FCI_CUDA(h, cudaMemcpyAsync(cp, c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            FCI_CUDA(h, cudaMemcpyAsync(scp, sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            FCI_CUDA(h, cudaStreamSynchronize(s));
+            have_prev = true;
+            E_prev = lam;
+            if (!(sqrt(tn2) >= 1e-10)) {  // new direction linearly dependent on the subspace
+                done = true;
+                break;
+            }
+            k_scale<<<vb, RED_THREADS, 0, s>>>(t, nreal, nrm);
+            FCI_CUDA(h, cudaMemcpyAsync(Vk(k), t, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            ask(REQ_APPEND, Vk(k), Sk(k));
+            return FCI_OK;
+        }
+        return FCI_OK;
+    }
+
+    int finish(void *C_out, double *energy, fci_davidson_log *lg) {
+        if (C_out) FCI_CUDA(h, cudaMemcpyAsync(C_out, c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+        FCI_CUDA(h, cudaStreamSynchronize(s));
+        if (energy) *energy = E_prev;
+        if (lg) {
+            const int m = std::min<int>((int)log.size(), lg->capacity);
+            if (lg->iters)
+                for (int i = 0; i < m; ++i) lg->iters[i] = log[i];
+            lg->n_iter = lg->iters ? m : 0;
+            lg->converged = converged ? 1 : 0;
+            lg->n_sigma = n_sigma;
+        }
+        if (!converged)
+            return fci_fail(h, FCI_ERR_NOT_CONVERGED, "Davidson did not converge in %d iterations", o.max_iter);
+        return FCI_OK;
+    }
+};
 
 size_t davidson_ws_bytes(const fci_context *h, const fci_davidson_opts *o) {
     const int64_t n = h->das_active ? h->das.n_det : h->ndet;
@@ -386,228 +677,55 @@ size_t davidson_ws_bytes(const fci_context *h, const fci_davidson_opts *o) {
 int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, double *energy, fci_davidson_log *log,
                  void *ws, size_t ws_bytes, cudaStream_t s) {
     (void)ws_bytes;
-    const int64_t n = h->das_active ? h->das.n_det : h->ndet;
-    const bool cplx = h->dtype == FCI_C128;
-    const size_t esz = cplx ? 16 : 8;
-    const int64_t nreal = cplx ? 2 * n : n;
-    const size_t vec = al((size_t)n * esz);
-    const int ms = o->max_subspace;
-    char *p = (char *)ws;
-    dav_ws w;
-    w.V = (double *)p; p += ms * vec;
-    w.S = (double *)p; p += ms * vec;
-    w.c = (double *)p; p += vec;
-    w.sc = (double *)p; p += vec;
-    w.cp = (double *)p; p += vec;
-    w.scp = (double *)p; p += vec;
-    w.t = (double *)p; p += vec;
-    w.diag = (double *)p; p += al((size_t)n * 8);
-    w.sig_ws = p;
-    size_t sig = sigma_ws_bytes(h, o->precision, o->n_slices);
-    if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, o->final_precision, o->final_slices));
-    w.sig_bytes = al(sig);
-    const int64_t ldv = (int64_t)(vec / esz);  // elements between consecutive subspace vectors
-
-    // small device scratch inside the handle's buffer
-    double *small = h->d_small;
-    double *partial = small;                                  // RED_BLOCKS * 2 * KMAX
-    double *Hs = partial + RED_BLOCKS * 2 * KMAX;             // 2 * KMAX * KMAX
-    double *dots = Hs + 2 * KMAX * KMAX;                      // 2 * KMAX
-    double *y = dots + 2 * KMAX;                              // 2 * KMAX
-    double *nrm = y + 2 * KMAX;                               // 4
-    dav_scalars *scal = (dav_scalars *)(nrm + 4);
-    int64_t *argmin = (int64_t *)(scal + 1);
-
-    const unsigned vb = (unsigned)std::min<int64_t>(RED_BLOCKS, std::max<int64_t>(1, ceil_div(n, RED_THREADS)));
-
-    auto multidot = [&](const double *Vb, int k, const double *x, double *out) -> cudaError_t {
-        if (cplx) k_multidot<true><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, x, n, partial);
-        else k_multidot<false><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, x, n, partial);
-        k_reduce_partial<<<1, 64, 0, s>>>(partial, vb, k, out);
-        return cudaGetLastError();
-    };
-    auto lincomb = [&](const double *Vb, int k, const double *yy, double scale, double *out, int acc) -> cudaError_t {
-        if (cplx) k_lincomb<true><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, yy, scale, n, out, acc);
-        else k_lincomb<false><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, k, yy, scale, n, out, acc);
-        return cudaGetLastError();
-    };
-    auto normalize = [&](double *x, double *n2out) -> cudaError_t {
-        k_norm2<<<vb, RED_THREADS, 0, s>>>(x, nreal, partial);
-        k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, n2out);
-        k_scale<<<vb, RED_THREADS, 0, s>>>(x, nreal, n2out);
-        return cudaGetLastError();
-    };
-    auto Vk = [&](int i) { return (double *)((char *)w.V + (size_t)i * vec); };
-    auto Sk = [&](int i) { return (double *)((char *)w.S + (size_t)i * vec); };
-    int n_sigma = 0;
-    int prec = o->precision, slices = o->n_slices;
-    bool final_phase = o->precision == FCI_PREC_FP64 ||
-                       (o->precision == o->final_precision && o->n_slices == o->final_slices);
-    auto sigma = [&](const double *x, double *out) -> int {
-        ++n_sigma;
-        return sigma_dispatch(h, x, out, prec, slices, w.sig_ws, w.sig_bytes, s);
-    };
-    // New subspace column k: Hs[:, k] = V^H S_k.
-    auto add_column = [&](int k) -> int {
-        FCI_CUDA(h, multidot(w.V, k + 1, Sk(k), dots));
-        k_hsub_update<<<1, 64, 0, s>>>(Hs, dots, k);
-        FCI_CUDA(h, cudaGetLastError());
-        return FCI_OK;
-    };
-
-    int rc;
-    FCI_CUDA(h, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     2 * (2 * KMAX) * (2 * KMAX + 1) * (int)sizeof(double)));
-    // diagonal and start vector
-    if (h->das_active) FCI_CUDA(h, launch_diag_das(h, w.diag, s));
-    else if (h->mode == FCI_MODE_SPINOR) FCI_CUDA(h, launch_diag_spinor(h, w.diag, s));
-    else FCI_CUDA(h, launch_diag_fci(h, w.diag, s));
-    if (o->use_guess) {
-        FCI_CUDA(h, cudaMemcpyAsync(Vk(0), C_io, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-    } else {
-        k_argmin<<<1, 256, 0, s>>>(w.diag, n, argmin);
-        k_set_unit<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, cplx, argmin);
+    fci_davidson_state st;
+    int rc = st.init(h, o, o->use_guess ? C_io : nullptr, ws, s);
+    while (!rc) {
+        rc = sigma_dispatch(h, st.req_x, st.req_y, st.prec, st.slices, st.sig_ws, st.sig_bytes, s);
+        if (rc) break;
+        if ((rc = st.consume_sigma())) break;
+        if ((rc = st.run_until_sigma())) break;
+        if (st.done) break;
     }
-    FCI_CUDA(h, normalize(Vk(0), nrm));
-    if ((rc = sigma(Vk(0), Sk(0)))) return rc;
-    FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
-    if ((rc = add_column(0))) return rc;
-    int k = 1;
-    bool have_prev = false;
-    bool converged = false;
-    double E_prev = 0.0;
-    int it_rec = 0;
-    int phase1_iters = 0;
-    dav_scalars hs{};
-    for (int it = 1; it <= o->max_iter; ++it) {
-        auto t0 = std::chrono::steady_clock::now();
-        {
-            const int m = cplx ? 2 * k : k;
-            k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, y, scal);
-        }
-        FCI_CUDA(h, lincomb(w.V, k, y, 1.0, w.c, 0));
-        FCI_CUDA(h, lincomb(w.S, k, y, 1.0, w.sc, 0));
-        if (have_prev) {
-            FCI_CUDA(h, multidot(w.cp, 1, w.c, dots));  // <c_prev|c>
-            FCI_CUDA(h, cudaMemcpyAsync(&scal->ov_re, dots, 16, cudaMemcpyDeviceToDevice, s));
-        }
-        if (cplx) k_residual<true><<<vb, RED_THREADS, 0, s>>>(w.c, w.sc, w.cp, have_prev, w.diag, scal, n, w.t, partial);
-        else k_residual<false><<<vb, RED_THREADS, 0, s>>>(w.c, w.sc, w.cp, have_prev, w.diag, scal, n, w.t, partial);
-        k_reduce_residual<<<1, 32, 0, s>>>(partial, vb, scal);
-        FCI_CUDA(h, cudaGetLastError());
-        FCI_CUDA(h, cudaMemcpyAsync(&hs, scal, sizeof hs, cudaMemcpyDeviceToHost, s));
-        FCI_CUDA(h, cudaStreamSynchronize(s));
-        const double lam = hs.lam, rn = sqrt(hs.rnorm2);
-        const double dE = it > 1 ? lam - E_prev : 0.0;
-        auto t1 = std::chrono::steady_clock::now();
-        if (log && log->iters && it_rec < log->capacity) {
-            fci_davidson_iter &r = log->iters[it_rec];
-            r.iteration = it;
-            r.precision = prec;
-            r.energy = lam;  // sigma already includes e_core C
-            r.delta_energy = dE;
-            r.max_delta_c = have_prev ? hs.maxdc : 0.0;
-            r.residual_norm = rn;
-            r.seconds = std::chrono::duration<double>(t1 - t0).count();
-        }
-        ++it_rec;
-        if (!isfinite(lam) || !isfinite(rn)) return fci_fail(h, FCI_ERR_CUDA, "Davidson produced a non-finite value");
-        if (!final_phase) {
-            ++phase1_iters;
-            if (rn <= o->switch_residual || phase1_iters >= o->max_iter / 2) {
-                // Residual correction: restart from the Ritz vector with the final precision.
-                final_phase = true;
-                prec = o->final_precision;
-                slices = o->final_slices;
-                FCI_CUDA(h, cudaMemcpyAsync(Vk(0), w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-                FCI_CUDA(h, normalize(Vk(0), nrm));
-                if ((rc = sigma(Vk(0), Sk(0)))) return rc;
-                FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
-                if ((rc = add_column(0))) return rc;
-                k = 1;
-                FCI_CUDA(h, cudaMemcpyAsync(w.cp, w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-                have_prev = true;
-                E_prev = lam;
-                continue;
-            }
-        } else if (rn <= o->tol_residual && it > 1 && fabs(dE) <= o->tol_energy) {
-            converged = true;
-            E_prev = lam;
-            break;
-        }
-        if (o->eps > 0.0) {
-            if (cplx) k_threshold<true><<<vb, RED_THREADS, 0, s>>>(w.t, n, scal, o->eps);
-            else k_threshold<false><<<vb, RED_THREADS, 0, s>>>(w.t, n, scal, o->eps);
-        }
-        if (k >= ms) {
-            // collapse to the current and previous Ritz vectors (sigma by linearity)
-            // V_0 = c / ||c||, S_0 = sc / ||c||
-            FCI_CUDA(h, cudaMemcpyAsync(Vk(0), w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-            FCI_CUDA(h, cudaMemcpyAsync(Sk(0), w.sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-            k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, partial);
-            k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
-            k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, nrm);
-            k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(0), nreal, nrm);
-            int knew = 1;
-            if (have_prev && ms > 2) {
-                // p = c_prev - <c|c_prev> c, S_p = sc_prev - <c|c_prev> sc, both / ||p||
-                // Two Gram-Schmidt passes: c and c_prev are nearly parallel near convergence,
-                // and one pass leaves an orthogonality error of eps / ||p|| that compounds
-                // over successive collapses.
-                FCI_CUDA(h, cudaMemcpyAsync(Vk(1), w.cp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-                FCI_CUDA(h, cudaMemcpyAsync(Sk(1), w.scp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-                for (int pass = 0; pass < 2; ++pass) {
-                    FCI_CUDA(h, multidot(Vk(0), 1, Vk(1), dots));
-                    k_negate<<<1, 64, 0, s>>>(dots, 1);
-                    FCI_CUDA(h, lincomb(Vk(0), 1, dots, 1.0, Vk(1), 1));
-                    FCI_CUDA(h, lincomb(Sk(0), 1, dots, 1.0, Sk(1), 1));
-                }
-                k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, partial);
-                k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
-                double pn2 = 0.0;
-                FCI_CUDA(h, cudaMemcpyAsync(&pn2, nrm, 8, cudaMemcpyDeviceToHost, s));
-                FCI_CUDA(h, cudaStreamSynchronize(s));
-                if (sqrt(pn2) > 1e-10) {
-                    k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, nrm);
-                    k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(1), nreal, nrm);
-                    knew = 2;
-                }
-            }
-            FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
-            for (int j = 0; j < knew; ++j)
-                if ((rc = add_column(j))) return rc;
-            k = knew;
-        }
-        // two rounds of classical Gram-Schmidt against V[0..k)
-        for (int round = 0; round < 2; ++round) {
-            FCI_CUDA(h, multidot(w.V, k, w.t, dots));
-            k_negate<<<1, 64, 0, s>>>(dots, k);
-            FCI_CUDA(h, lincomb(w.V, k, dots, 1.0, w.t, 1));
-        }
-        k_norm2<<<vb, RED_THREADS, 0, s>>>(w.t, nreal, partial);
-        k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
-        double tn2 = 0.0;
-        FCI_CUDA(h, cudaMemcpyAsync(&tn2, nrm, 8, cudaMemcpyDeviceToHost, s));
-        FCI_CUDA(h, cudaMemcpyAsync(w.cp, w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-        FCI_CUDA(h, cudaMemcpyAsync(w.scp, w.sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-        FCI_CUDA(h, cudaStreamSynchronize(s));
-        have_prev = true;
-        E_prev = lam;
-        if (!(sqrt(tn2) >= 1e-10)) break;  // new direction linearly dependent on the subspace
-        k_scale<<<vb, RED_THREADS, 0, s>>>(w.t, nreal, nrm);
-        FCI_CUDA(h, cudaMemcpyAsync(Vk(k), w.t, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-        if ((rc = sigma(Vk(k), Sk(k)))) return rc;
-        if ((rc = add_column(k))) return rc;
-        ++k;
+    if (rc) return rc;
+    return st.finish(C_io, energy, log);
+}
+
+// ------------------------------------------------------------------ step-wise ABI
+
+int davidson_state_begin(fci_context *h, const fci_davidson_opts *o, const void *guess, void *ws, cudaStream_t s,
+                         fci_davidson_state **out) {
+    fci_davidson_state *st = new (std::nothrow) fci_davidson_state();
+    if (!st) return fci_fail(h, FCI_ERR_OOM, "host allocation failed");
+    int rc = st->init(h, o, guess, ws, s);
+    if (rc) {
+        delete st;
+        return rc;
     }
-    FCI_CUDA(h, cudaMemcpyAsync(C_io, w.c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-    FCI_CUDA(h, cudaStreamSynchronize(s));
-    *energy = E_prev;
-    if (log) {
-        log->n_iter = std::min(it_rec, log->capacity);
-        log->converged = converged ? 1 : 0;
-        log->n_sigma = n_sigma;
-    }
-    if (!converged) return fci_fail(h, FCI_ERR_NOT_CONVERGED, "Davidson did not converge in %d iterations", o->max_iter);
+    *out = st;
     return FCI_OK;
 }
+
+int davidson_state_advance(fci_davidson_state *st, int *done) {
+    int rc = st->consume_sigma();
+    if (!rc) rc = st->run_until_sigma();
+    *done = st->done ? 1 : 0;
+    return rc;
+}
+
+void davidson_state_request(const fci_davidson_state *st, const void **x, void **y, int *prec, int *slices,
+                            void **sig_ws, size_t *sig_bytes) {
+    if (x) *x = st->req_x;
+    if (y) *y = st->req_y;
+    if (prec) *prec = st->prec;
+    if (slices) *slices = st->slices;
+    if (sig_ws) *sig_ws = st->sig_ws;
+    if (sig_bytes) *sig_bytes = st->sig_bytes;
+}
+
+int davidson_state_finish(fci_davidson_state *st, void *C_out, double *energy, fci_davidson_log *log) {
+    const int rc = st->finish(C_out, energy, log);
+    delete st;
+    return rc;
+}
+
+fci_context *davidson_state_handle(const fci_davidson_state *st) { return st->h; }

@@ -100,7 +100,13 @@ static int set_dev(fci_context *h) {
     return FCI_OK;
 }
 
+static void drop_graphs(fci_context *h) {
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
 static void free_strings(fci_context *h) {
+    drop_graphs(h);
     fci_dev_free(h->d_str_a); fci_dev_free(h->d_str_b);
     fci_dev_free(h->d_rep_a); fci_dev_free(h->d_rep_b);
     fci_dev_free(h->d_pair_a); fci_dev_free(h->d_pair_b);
@@ -213,6 +219,7 @@ int fci_destroy(fci_handle h) {
     cudaSetDevice(h->device);
     drain_events(h);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
+    drop_graphs(h);
     free_strings(h);
     fci_dev_free(h->d_binom);
     fci_dev_free(h->d_small);
@@ -533,6 +540,148 @@ int davidson_solve(fci_handle h, const fci_davidson_opts *o, void *C_io, double 
     rc = set_dev(h);
     if (rc) return rc;
     return davidson_run(h, o, (double *)C_io, energy, log, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int fci_clear_graphs(fci_handle h) {
+    if (!h) return fci_fail(nullptr, FCI_ERR_ARG, "NULL handle");
+    cudaSetDevice(h->device);
+    drop_graphs(h);
+    return FCI_OK;
+}
+
+int fci_sigma_graph(fci_handle h, const void *C, void *sigma, int precision, int n_slices, void *ws, size_t ws_bytes,
+                    fci_stream stream) {
+    if (!h) return fci_fail(nullptr, FCI_ERR_ARG, "NULL handle");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (auto &g : h->graphs) {
+        if (g.C == C && g.sigma == sigma && g.precision == precision && g.n_slices == n_slices && g.ws == ws &&
+            g.stream == s) {
+            FCI_CUDA(h, cudaSetDevice(h->device));
+            FCI_CUDA(h, cudaGraphLaunch(g.exec, s));
+            return FCI_OK;
+        }
+    }
+    // first call: a plain run (prepares integrals, kernel attributes), then the capture
+    int rc = fci_sigma(h, C, sigma, 1, precision, n_slices, ws, ws_bytes, stream);
+    if (rc) return rc;
+    if (s == nullptr) return FCI_OK;  // the legacy default stream cannot be captured
+    const bool timing = h->timing;
+    h->timing = false;
+    cudaGraph_t graph = nullptr;
+    FCI_CUDA(h, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    rc = sigma_dispatch(h, C, sigma, precision, n_slices, ws, ws_bytes, s);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    h->timing = timing;
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fci_cuda_check(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fci_cuda_check(h, e, "cudaGraphInstantiate");
+    if (h->graphs.size() >= 64) {
+        cudaGraphExecDestroy(h->graphs.front().exec);
+        h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back({C, sigma, precision, n_slices, ws, s, exec});
+    return FCI_OK;
+}
+
+int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream) {
+    if (!jobs || n_jobs < 0) return fci_fail(nullptr, FCI_ERR_ARG, "bad job list");
+    if (n_jobs == 0) return FCI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    // validate every job first
+    for (int i = 0; i < n_jobs; ++i) {
+        const fci_sigma_job &j = jobs[i];
+        fci_context *h = j.handle;
+        if (!h) return fci_fail(nullptr, FCI_ERR_ARG, "job %d has no handle", i);
+        if (h->device != jobs[0].handle->device) return fci_fail(h, FCI_ERR_ARG, "jobs on different devices");
+        for (int k = 0; k < i; ++k)
+            if (jobs[k].handle == h) return fci_fail(h, FCI_ERR_ARG, "handle appears in jobs %d and %d", k, i);
+        if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "job %d: no strings built", i);
+        if (!j.C || !j.sigma) return fci_fail(h, FCI_ERR_ARG, "job %d: NULL vector", i);
+        if (j.precision != FCI_PREC_FP64 && j.precision != FCI_PREC_OZ_BF16)
+            return fci_fail(h, FCI_ERR_ARG, "job %d: unknown precision", i);
+        if (j.precision == FCI_PREC_OZ_BF16 && (j.n_slices < 2 || j.n_slices > 8 || h->dtype != FCI_R64))
+            return fci_fail(h, FCI_ERR_ARG, "job %d: bad split-precision request", i);
+        const size_t need = sigma_ws_bytes(h, j.precision, j.n_slices);
+        if (j.workspace_bytes < need || !j.workspace || ((uintptr_t)j.workspace & 255))
+            return fci_fail(h, FCI_ERR_ARG, "job %d: workspace too small or misaligned", i);
+    }
+    FCI_CUDA(jobs[0].handle, cudaSetDevice(jobs[0].handle->device));
+    std::vector<char> done(n_jobs, 0);
+    // split-precision FCI jobs, grouped by slice count: one contraction launch per group
+    for (int i = 0; i < n_jobs; ++i) {
+        const fci_sigma_job &j = jobs[i];
+        if (done[i] || j.precision != FCI_PREC_OZ_BF16 || j.handle->mode != FCI_MODE_FCI || j.handle->das_active)
+            continue;
+        std::vector<fci_context *> hs;
+        std::vector<const double *> Cs;
+        std::vector<double *> ss;
+        std::vector<void *> ws;
+        for (int k = i; k < n_jobs; ++k) {
+            const fci_sigma_job &q = jobs[k];
+            if (done[k] || q.precision != FCI_PREC_OZ_BF16 || q.n_slices != j.n_slices ||
+                q.handle->mode != FCI_MODE_FCI || q.handle->das_active)
+                continue;
+            hs.push_back(q.handle);
+            Cs.push_back((const double *)q.C);
+            ss.push_back((double *)q.sigma);
+            ws.push_back(q.workspace);
+            done[k] = 1;
+        }
+        int rc = oz_sigma_group(hs.data(), Cs.data(), ss.data(), ws.data(), (int)hs.size(), j.n_slices, s);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < n_jobs; ++i) {
+        if (done[i]) continue;
+        const fci_sigma_job &j = jobs[i];
+        int rc = sigma_dispatch(j.handle, j.C, j.sigma, j.precision, j.n_slices, j.workspace, j.workspace_bytes, s);
+        if (rc) return rc;
+    }
+    return FCI_OK;
+}
+
+int davidson_begin(fci_handle h, const fci_davidson_opts *o, const void *C_guess, void *ws, size_t ws_bytes,
+                   fci_stream stream, fci_davidson_handle *out) {
+    if (!h || !out) return fci_fail(h, FCI_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    int rc = check_opts(h, o);
+    if (rc) return rc;
+    if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "no strings built");
+    if ((o->precision == FCI_PREC_OZ_BF16 || o->final_precision == FCI_PREC_OZ_BF16) && h->dtype != FCI_R64)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real integrals only");
+    const size_t need = davidson_ws_bytes(h, o);
+    if (ws_bytes < need || !ws) return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes", ws_bytes, need);
+    if (((uintptr_t)ws & 255) != 0) return fci_fail(h, FCI_ERR_ARG, "workspace not 256-byte aligned");
+    rc = set_dev(h);
+    if (rc) return rc;
+    return davidson_state_begin(h, o, C_guess, ws, (cudaStream_t)stream, out);
+}
+
+int davidson_request(fci_davidson_handle st, const void **x, void **y, int *precision, int *n_slices, void **sws,
+                     size_t *sws_bytes) {
+    if (!st) return fci_fail(nullptr, FCI_ERR_ARG, "NULL Davidson state");
+    davidson_state_request(st, x, y, precision, n_slices, sws, sws_bytes);
+    return FCI_OK;
+}
+
+int davidson_advance(fci_davidson_handle st, int *done) {
+    if (!st || !done) return fci_fail(nullptr, FCI_ERR_ARG, "NULL argument");
+    fci_context *h = davidson_state_handle(st);
+    int rc = set_dev(h);
+    if (rc) return rc;
+    return davidson_state_advance(st, done);
+}
+
+int davidson_finish(fci_davidson_handle st, void *C_out, double *energy, fci_davidson_log *log) {
+    if (!st) return fci_fail(nullptr, FCI_ERR_ARG, "NULL Davidson state");
+    fci_context *h = davidson_state_handle(st);
+    set_dev(h);
+    return davidson_state_finish(st, C_out, energy, log);
 }
 
 int fci_table_bytes(fci_handle h, int table, size_t *bytes) {

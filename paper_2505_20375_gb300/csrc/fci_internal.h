@@ -106,6 +106,17 @@ struct fci_context {
     double phase_ms[FCI_N_PHASES] = {0, 0, 0, 0};
     int64_t phase_launches[FCI_N_PHASES] = {0, 0, 0, 0};
 
+    // CUDA graphs of sigma builds, keyed by their arguments
+    struct graph_rec {
+        const void *C;
+        void *sigma;
+        int precision, n_slices;
+        void *ws;
+        cudaStream_t stream;
+        cudaGraphExec_t exec;
+    };
+    std::vector<graph_rec> graphs;
+
     // device status word of the last split-precision sigma (inside the caller's workspace)
     int *last_status = nullptr;
 
@@ -180,8 +191,18 @@ int oz_prepare_G(fci_context *h, int n_slices);
 size_t oz_workspace_bytes(const fci_context *h, int n_slices);
 int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int n_slices, void *ws,
                  size_t ws_bytes, cudaStream_t s);
+int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
+                   int s, cudaStream_t st);
 
 // davidson.cu
+struct fci_davidson_state;
+int davidson_state_begin(fci_context *h, const fci_davidson_opts *o, const void *guess, void *ws, cudaStream_t s,
+                         fci_davidson_state **out);
+int davidson_state_advance(fci_davidson_state *st, int *done);
+void davidson_state_request(const fci_davidson_state *st, const void **x, void **y, int *prec, int *slices,
+                            void **sig_ws, size_t *sig_bytes);
+int davidson_state_finish(fci_davidson_state *st, void *C_out, double *energy, fci_davidson_log *log);
+fci_context *davidson_state_handle(const fci_davidson_state *st);
 int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, double *energy,
                  fci_davidson_log *log, void *ws, size_t ws_bytes, cudaStream_t s);
 size_t davidson_ws_bytes(const fci_context *h, const fci_davidson_opts *o);

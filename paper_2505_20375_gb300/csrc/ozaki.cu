@@ -18,18 +18,21 @@
 //   sigma_I = 2^{8 L0 - sh_G - sh_C} sum <I|E_pq|K> E_int[pq, K] + e_core C_I.
 // (Methods, Eqs. sigmaL/sigmaL2e: E = g' D is the dense contraction of the sigma build.)
 //
-// Kernel layout (one persistent CTA per SM, 544 threads):
-//   warps 0-7  producers: gather D_int for a tile of 32 determinants from the fixed-point
+// Kernel layout (one persistent CTA per SM, 512 threads, one job per CTA; a grouped
+// launch shares the CTAs among several sigma builds in proportion to their tiles):
+//   warps 0-6  producers: gather D_int for a tile of 64 determinants from the fixed-point
 //              C and the pair tables, keep it in registers, and write its s digit planes
-//              (f16, canonical K-major core-matrix layout) into a 3-slot shared ring;
-//   warps 8-15 epilogue: read the s level accumulators of a tile from TMEM (two warps per
-//              32-lane quadrant, 16 columns each), combine them in int64, store E_int rows;
-//   warp 16    allocates TMEM; lane 0 issues tcgen05.mma (M = 128 pair rows of G digits
-//              resident in shared memory, N = 32 determinants, K = 16 per instruction) and
+//              (f16, canonical K-major core-matrix layout) into a 2- or 3-slot shared ring;
+//   warps 7-14 epilogue: read the s level accumulators of a tile from TMEM (two warps per
+//              32-lane quadrant, 32 columns each, in chunks of 16), combine them in int64,
+//              store E_int in a tile-major layout;
+//   warp 15    allocates TMEM; lane 0 issues tcgen05.mma (M = 128 pair rows of G digits
+//              resident in shared memory, N = 64 determinants, K = 16 per instruction) and
 //              tcgen05.commit to the mbarriers that hand buffers between the roles.
-// Level accumulators are double-buffered (2 x s x 32 TMEM columns).  Every wait on an
-// mbarrier is bounded in time; on expiry the kernel records FCI_ERR_TIMEOUT in a device
-// status word, stops issuing work, drains the MMAs it issued, frees TMEM and returns.
+// Level accumulators take s x 64 TMEM columns, double-buffered when 2 s x 64 <= 512.
+// Every wait on an mbarrier is bounded in time; on expiry the kernel records
+// FCI_ERR_TIMEOUT in a device status word, stops issuing work, drains the MMAs it issued,
+// frees TMEM and returns.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -42,10 +45,10 @@
 
 namespace {
 
-constexpr int OZ_PRODUCER_WARPS = 8;
+constexpr int OZ_PRODUCER_WARPS = 7;  // 16 warps in all: up to 128 registers per thread
 constexpr int OZ_EPILOGUE_WARPS = 8;  // two per TMEM lane quadrant, 16 columns each
 constexpr int OZ_MMA_WARP = OZ_PRODUCER_WARPS + OZ_EPILOGUE_WARPS;
-constexpr int OZ_THREADS = 32 * (OZ_MMA_WARP + 1);  // 544
+constexpr int OZ_THREADS = 32 * (OZ_MMA_WARP + 1);  // 512
 constexpr int OZ_MAX_RING = 3;  // digit-plane slots (2 or 3, whatever shared memory allows)
 // Determinants per tile (the MMA's N).  A tcgen05.mma costs at least ~45 cycles to issue
 // whatever its size, so an M=128 N=32 K=16 MMA reaches only about a third of the tensor
@@ -69,6 +72,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Same test, but a thread whose phase is not complete may be suspended (up to the hint,
+// in ns) instead of returning at once, so waiting warps stop competing for issue slots.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity), "r"(20000u)
         : "memory");
     return ok != 0;
 }
@@ -154,6 +168,15 @@ struct OzParams {
     int ring;  // digit-plane slots in use
 };
 
+// Several sigma builds in one launch: CTAs [cta_start[j], cta_start[j+1]) serve job j.
+// Passed by value (kernel parameter space), so the launch needs no device-side table.
+constexpr int OZ_MAX_JOBS = 32;
+struct OzGroup {
+    int n_jobs;
+    int cta_start[OZ_MAX_JOBS + 1];
+    OzParams job[OZ_MAX_JOBS];
+};
+
 // Warp-uniform variant: lane 0 waits, every lane gets the same answer, so no lane can
 // leave a loop that the others continue (the tcgen05.ld/alloc forms are .sync.aligned).
 __device__ __forceinline__ bool oz_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
@@ -172,8 +195,8 @@ __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, volatile 
                                         long long timeout) {
     const long long t0 = clock64();
     int spins = 0;
-    while (!mbar_try_wait(bar, parity)) {
-        if (((++spins) & 63) == 0) {
+    while (!mbar_try_wait_sleep(bar, parity)) {
+        if (((++spins) & 3) == 0) {
             if (*abort) return false;
             if (clock64() - t0 > timeout) {
                 *abort = 1;
@@ -195,7 +218,19 @@ __device__ __forceinline__ bool oz_wait_warp(uint32_t bar, uint32_t parity, vola
 // S: slices per operand; NT: determinants per tile (the MMA's N).  Accumulators are
 // double-buffered when 2 x S x NT TMEM columns fit in 512, single-buffered otherwise.
 template <int S, int NT>
-__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_constant__ OzGroup grp) {
+    // this CTA's job, and its place among the CTAs of that job
+    // (the job's parameters are copied to shared memory once; roles read them there)
+    __shared__ OzParams p;
+    __shared__ int64_t cta_lo, cta_n;
+    if (threadIdx.x == 0) {
+        int jb = 0;
+        while (jb + 1 < grp.n_jobs && (int)blockIdx.x >= grp.cta_start[jb + 1]) ++jb;
+        p = grp.job[jb];
+        cta_lo = grp.cta_start[jb];
+        cta_n = grp.cta_start[jb + 1] - grp.cta_start[jb];
+    }
+    __syncthreads();
     constexpr int NBUF = (2 * S * NT <= 512) ? 2 : 1;
     constexpr int PT = 32 * OZ_PRODUCER_WARPS;
     constexpr int UNITS = (NT * 16 + PT - 1) / PT;  // producer units per thread (KC <= 16)
@@ -241,14 +276,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
     // Each CTA takes one contiguous range of tiles, so consecutive tiles of a CTA share
     // alpha strings and read the same rows of C (cache and TLB locality).
     const int64_t ntiles = (p.N + NT - 1) / NT;
-    const int64_t t_begin = ntiles * blockIdx.x / gridDim.x, t_end = ntiles * (blockIdx.x + 1) / gridDim.x;
+    const int64_t cta = (int64_t)blockIdx.x - cta_lo;
+    const int64_t t_begin = ntiles * cta / cta_n, t_end = ntiles * (cta + 1) / cta_n;
 
     if (warp < OZ_PRODUCER_WARPS) {
         // ---------------------------------------------------------------- producers
-        // Thread t owns units (det r, K-core c) t, t + 256, ... of the tile: 8 pair
+        // Thread t owns units (det r, K-core c) t, t + 224, ... of the tile: 8 pair
         // indices rs = 8c..8c+7 of one determinant.  The pair tables have rows up to the
         // padded K, filled with -1, so no range test is needed.
-        const int t = threadIdx.x;  // 0..255
+        const int t = threadIdx.x;  // 0..223
         const int units = NT * KC;
         constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
         uint32_t q = 0;
@@ -315,8 +351,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(OzParams p) {
         // ---------------------------------------------------------------- epilogue
         // Warp (quadrant qd, half h) reads lanes 32 qd .. 32 qd + 31 and columns
         // [h NT/2, (h+1) NT/2) in chunks of 16, every level of a chunk into int64.
+        // A warp may only access the TMEM lane quadrant warp_id % 4; the two warps of a
+        // quadrant split the tile's columns.
         const int ew = warp - OZ_PRODUCER_WARPS;
-        const int qd = ew & 3;
+        const int qd = warp & 3;
         const int cbeg = (NT / 2) * (ew >> 2);
         const int row = 32 * qd + lane;
         constexpr int lowshift = 8 * (L0 - (S - 1));
@@ -567,13 +605,14 @@ size_t oz_workspace_bytes(const fci_context *h, int s) {
     return al256((size_t)h->ndet * 8) + al256((size_t)ntiles * h->npair * OZ_TILE * 8) + 256;
 }
 
-int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws, size_t ws_bytes, cudaStream_t st) {
-    (void)ws_bytes;
+// Fixed-point conversion of C and the job's kernel parameters (first half of a split sigma).
+static int oz_prepare_job(fci_context *h, const double *C, int s, void *ws, cudaStream_t st, OzParams &prm,
+                          int64_t **E_out, int **shC_out, int **status_out) {
     if (h->mode != FCI_MODE_FCI) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision needs alpha/beta strings");
     int rc = oz_prepare_G(h, s);
     if (rc) return rc;
     const int KC = oz_kc(h);
-    const int64_t N = h->ndet, ldE = (N + 31) / 32 * 32;
+    const int64_t N = h->ndet;
     char *p = (char *)ws;
     int64_t *Cint = (int64_t *)p;
     p += al256((size_t)N * 8);
@@ -591,7 +630,6 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
         k_to_fixed<<<nb, 256, 0, st>>>(C, N, s, maxbits, Cint, shC);
         FCI_CUDA(h, cudaGetLastError());
     }
-    OzParams prm;
     prm.N = N;
     prm.nsa = h->nsa;
     prm.nsb = h->nsb;
@@ -605,7 +643,7 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
     prm.Cint = Cint;
     prm.Gimg = (const uint4 *)h->d_Gs;
     prm.E = E;
-    prm.ldE = ldE;
+    prm.ldE = 0;
     prm.status = status;
     const char *to = getenv("FCI_WAIT_TIMEOUT_MS");
     const double ms = to ? atof(to) : 2000.0;
@@ -613,8 +651,14 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
     const char *stall = getenv("FCI_TEST_STALL_PRODUCER");
     prm.stall_test = stall ? atoi(stall) : 0;
     prm.ring = oz_ring(s, KC);
-    const size_t smem = oz_smem_bytes(s, KC, prm.ring);
-    void (*kern)(OzParams) = nullptr;
+    *E_out = E;
+    *shC_out = shC;
+    *status_out = status;
+    return FCI_OK;
+}
+
+static int oz_launch_group(fci_context *h, const OzGroup &grp, int s, size_t smem, cudaStream_t st) {
+    void (*kern)(const OzGroup) = nullptr;
     switch (s) {
         case 2: kern = k_oz_contract<2, OZ_TILE>; break;
         case 3: kern = k_oz_contract<3, OZ_TILE>; break;
@@ -625,22 +669,89 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
         default: return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d", s);
     }
     FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
+    kern<<<grp.cta_start[grp.n_jobs], OZ_THREADS, smem, st>>>(grp);
+    FCI_CUDA(h, cudaGetLastError());
+    return FCI_OK;
+}
+
+static int oz_finish_job(fci_context *h, const double *C, double *sigma, const OzParams &prm, int64_t *E, int *shC,
+                         int *status, cudaStream_t st) {
+    phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
+    const int threads = 128;
+    dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
+    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, h->d_pair_a, h->d_pair_b, E, 0, C, h->e_core,
+                                       8 * prm.L0 - h->G_exp, shC, status, sigma);
+    FCI_CUDA(h, cudaGetLastError());
+    return FCI_OK;
+}
+
+static int oz_num_sms(fci_context *h, int *nsm) {
+    FCI_CUDA(h, cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, h->device));
+    return FCI_OK;
+}
+
+int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws, size_t ws_bytes, cudaStream_t st) {
+    (void)ws_bytes;
+    OzGroup grp;
+    int64_t *E;
+    int *shC, *status;
+    int rc = oz_prepare_job(h, C, s, ws, st, grp.job[0], &E, &shC, &status);
+    if (rc) return rc;
     int nsm = 0;
-    FCI_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const int64_t ntiles = (N + OZ_TILE - 1) / OZ_TILE;
-    const unsigned grid = (unsigned)std::min<int64_t>(nsm, ntiles);
-    {
-        phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
-        kern<<<grid, OZ_THREADS, smem, st>>>(prm);
-        FCI_CUDA(h, cudaGetLastError());
-    }
-    {
-        phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
-        const int threads = 128;
-        dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
-        k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, h->d_pair_a, h->d_pair_b, E, ldE, C,
-                                           h->e_core, 8 * prm.L0 - h->G_exp, shC, status, sigma);
-        FCI_CUDA(h, cudaGetLastError());
+    if ((rc = oz_num_sms(h, &nsm))) return rc;
+    const int64_t ntiles = (h->ndet + OZ_TILE - 1) / OZ_TILE;
+    grp.n_jobs = 1;
+    grp.cta_start[0] = 0;
+    grp.cta_start[1] = (int)std::min<int64_t>(nsm, ntiles);
+    if ((rc = oz_launch_group(h, grp, s, oz_smem_bytes(s, grp.job[0].KC, grp.job[0].ring), st))) return rc;
+    return oz_finish_job(h, C, sigma, grp.job[0], E, shC, status, st);
+}
+
+// Split-precision sigma of several problems sharing one slice count: one fixed-point
+// pre-pass per job, ONE persistent contraction launch for all jobs (CTAs shared in
+// proportion to tiles, at least one per job), one scatter per job.
+int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
+                   int s, cudaStream_t st) {
+    int nsm = 0;
+    int rc = oz_num_sms(hs[0], &nsm);
+    if (rc) return rc;
+    for (int base = 0; base < n;) {
+        const int m = std::min({n - base, OZ_MAX_JOBS, nsm});
+        OzGroup grp;
+        int64_t *E[OZ_MAX_JOBS];
+        int *shC[OZ_MAX_JOBS], *status[OZ_MAX_JOBS];
+        size_t smem = 0;
+        int64_t tiles[OZ_MAX_JOBS], total = 0;
+        for (int j = 0; j < m; ++j) {
+            fci_context *h = hs[base + j];
+            if ((rc = oz_prepare_job(h, Cs[base + j], s, wss[base + j], st, grp.job[j], &E[j], &shC[j], &status[j])))
+                return rc;
+            smem = std::max(smem, oz_smem_bytes(s, grp.job[j].KC, grp.job[j].ring));
+            tiles[j] = (h->ndet + OZ_TILE - 1) / OZ_TILE;
+            total += tiles[j];
+        }
+        // CTAs in proportion to tiles, at least one per job, never more CTAs than tiles
+        int ctas[OZ_MAX_JOBS], used = 0;
+        for (int j = 0; j < m; ++j) {
+            ctas[j] = (int)std::max<int64_t>(1, std::min<int64_t>(tiles[j], (int64_t)(nsm - m) * tiles[j] / total + 1));
+            used += ctas[j];
+        }
+        while (used > nsm) {  // trim the largest shares
+            int jmax = 0;
+            for (int j = 1; j < m; ++j) if (ctas[j] > ctas[jmax]) jmax = j;
+            if (ctas[jmax] <= 1) break;
+            --ctas[jmax];
+            --used;
+        }
+        grp.n_jobs = m;
+        grp.cta_start[0] = 0;
+        for (int j = 0; j < m; ++j) grp.cta_start[j + 1] = grp.cta_start[j] + ctas[j];
+        if ((rc = oz_launch_group(hs[base], grp, s, smem, st))) return rc;
+        for (int j = 0; j < m; ++j)
+            if ((rc = oz_finish_job(hs[base + j], Cs[base + j], sigmas[base + j], grp.job[j], E[j], shC[j], status[j], st)))
+                return rc;
+        base += m;
     }
     return FCI_OK;
 }

@@ -86,6 +86,21 @@ _tcopy = _sig("fci_copy_table", [_vp, _i32, _vp, _sz, _vp])
 _set_timing = _sig("fci_set_phase_timing", [_vp, _i32])
 _get_times = _sig("fci_get_phase_times", [_vp, ctypes.POINTER(_dbl), ctypes.POINTER(_i64), _i32])
 _sync_status = _sig("fci_sync_status", [_vp, _vp])
+_sigma_graph = _sig("fci_sigma_graph", [_vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp])
+_clear_graphs = _sig("fci_clear_graphs", [_vp])
+
+
+class fci_sigma_job(ctypes.Structure):
+    _fields_ = [("handle", _vp), ("C", _vp), ("sigma", _vp), ("precision", _i32), ("n_slices", _i32),
+                ("workspace", _vp), ("workspace_bytes", _sz)]
+
+
+_sigma_grouped = _sig("fci_sigma_grouped", [ctypes.POINTER(fci_sigma_job), _i32, _vp])
+_dav_begin = _sig("davidson_begin", [_vp, ctypes.POINTER(fci_davidson_opts), _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)])
+_dav_request = _sig("davidson_request", [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i32),
+                                         ctypes.POINTER(_i32), ctypes.POINTER(_vp), ctypes.POINTER(_sz)])
+_dav_advance = _sig("davidson_advance", [_vp, ctypes.POINTER(_i32)])
+_dav_finish = _sig("davidson_finish", [_vp, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(fci_davidson_log)])
 PHASES = ("gather", "contract", "scatter", "other")
 
 
@@ -209,6 +224,8 @@ class FCI:
 
     def _workspace(self, nbytes: int):
         if self._ws is None or self._ws_bytes < nbytes:
+            if self._ws is not None:
+                _clear_graphs(self._h)  # cached graphs name the old buffer
             self._ws = None
             self._ws = _alloc(nbytes, self.device)
             self._ws_ptr = _aligned_ptr(self._ws)
@@ -236,6 +253,34 @@ class FCI:
             dst.copy_(res, non_blocking=False)
             return dst
         return res
+
+    def sigma_graph(self, C: torch.Tensor, out: torch.Tensor, precision: str = "fp64", n_slices: int = 0,
+                    stream=None) -> torch.Tensor:
+        """sigma = H C for one device vector through a cached CUDA graph (fci_sigma_graph)."""
+        p, nb = self._workspace(self.sigma_workspace_bytes(precision, n_slices))
+        self._check(_sigma_graph(self._h, C.data_ptr(), out.data_ptr(), PRECISIONS[precision], n_slices, p, nb,
+                                 _stream(stream)))
+        return out
+
+    def clear_graphs(self):
+        self._check(_clear_graphs(self._h))
+
+    def davidson_opts(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
+                      precision="fp64", n_slices=6, switch_residual=1e-5, final_precision="fp64", final_slices=0,
+                      use_guess=False) -> fci_davidson_opts:
+        o = fci_davidson_opts()
+        _dav_defaults(ctypes.byref(o))
+        o.max_iter, o.max_subspace = max_iter, max_subspace
+        o.tol_residual, o.tol_energy, o.eps = tol_residual, tol_energy, eps
+        o.precision, o.n_slices, o.switch_residual = PRECISIONS[precision], n_slices, switch_residual
+        o.final_precision, o.final_slices = PRECISIONS[final_precision], final_slices
+        o.use_guess = 1 if use_guess else 0
+        return o
+
+    def davidson_workspace_bytes(self, opts: fci_davidson_opts) -> int:
+        b = _sz()
+        self._check(_dav_ws(self._h, ctypes.byref(opts), ctypes.byref(b)))
+        return b.value
 
     def davidson(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                  precision="fp64", n_slices=6, switch_residual=1e-5, guess: torch.Tensor = None,
@@ -289,3 +334,63 @@ class FCI:
         self._check(_tcopy(self._h, t, out.data_ptr(), b.value, _stream()))
         torch.cuda.current_stream().synchronize()
         return out
+
+
+# ---------------------------------------------------------------- batched steps
+
+def sigma_grouped(jobs, stream=None):
+    """jobs: list of (FCI, C, sigma, precision, n_slices, workspace_ptr, workspace_bytes);
+    one fci_sigma_grouped call (split-precision jobs share one contraction launch)."""
+    arr = (fci_sigma_job * len(jobs))()
+    for i, (f, C, out, prec, sl, ws, wsb) in enumerate(jobs):
+        arr[i] = fci_sigma_job(f._h, _vp(C if isinstance(C, int) else C.data_ptr()),
+                               _vp(out if isinstance(out, int) else out.data_ptr()),
+                               PRECISIONS[prec] if isinstance(prec, str) else prec, sl, _vp(ws), wsb)
+    rc = _sigma_grouped(arr, len(jobs), _stream(stream))
+    if rc:
+        raise FCIError(rc, last_error(None) or last_error(jobs[0][0]._h))
+
+
+class DavidsonStepper:
+    """Step-wise Davidson over the C ABI (davidson_begin/request/advance/finish): the
+    caller computes y = H x for each request, e.g. for many solves with one grouped call."""
+
+    def __init__(self, f: FCI, opts: fci_davidson_opts, guess: torch.Tensor = None, stream=None):
+        self.f = f
+        self.stream = stream
+        nbytes = f.davidson_workspace_bytes(opts)
+        self._ws = _alloc(nbytes, f.device)  # caller-owned, kept alive by this object
+        self._ws_ptr = _aligned_ptr(self._ws)
+        self._nbytes = nbytes
+        self.opts = opts
+        st = _vp()
+        g = _vp(guess.data_ptr()) if guess is not None else None
+        f._check(_dav_begin(f._h, ctypes.byref(opts), g, _vp(self._ws_ptr), nbytes, _stream(stream), ctypes.byref(st)))
+        self._st = st
+        self.done = False
+
+    def request(self):
+        x, y, ws = _vp(), _vp(), _vp()
+        prec, sl = _i32(), _i32()
+        wsb = _sz()
+        self.f._check(_dav_request(self._st, ctypes.byref(x), ctypes.byref(y), ctypes.byref(prec), ctypes.byref(sl),
+                                   ctypes.byref(ws), ctypes.byref(wsb)))
+        return x.value, y.value, prec.value, sl.value, ws.value, wsb.value
+
+    def advance(self):
+        d = _i32()
+        self.f._check(_dav_advance(self._st, ctypes.byref(d)))
+        self.done = bool(d.value)
+        return self.done
+
+    def finish(self, max_log=400):
+        C = torch.empty(self.f.n_det, dtype=self.f.vector_dtype(), device=self.f.device)
+        iters = (fci_davidson_iter * max_log)()
+        log = fci_davidson_log(0, 0, 0, max_log, ctypes.cast(iters, ctypes.POINTER(fci_davidson_iter)))
+        E = _dbl()
+        rc = _dav_finish(self._st, C.data_ptr(), ctypes.byref(E), ctypes.byref(log))
+        self._st = None
+        if rc not in (FCI_OK, FCI_ERR_NOT_CONVERGED):
+            self.f._check(rc)
+        its = [{k: getattr(iters[i], k) for k, _ in fci_davidson_iter._fields_} for i in range(log.n_iter)]
+        return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its)
