@@ -43,6 +43,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serving-requests", type=int, default=32,
+                    help="requests of the serving run (0 = skip); 256 is the full request stream")
+    ap.add_argument("--serving-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -266,6 +269,22 @@ def run_ours(a, rank, world, local_rank):
                 d["energy_error_vs_fp64"] = abs(d["energy"] - e64)
                 d["speedup_vs_fp64"] = davidson["fp64"]["seconds"] / d["seconds"]
 
+    # continuous-batching serving: a Poisson stream of Davidson requests (FCI (6e,6o) ..
+    # (12e,12o) and 16-orbital 4-space DAS), half of them in mixed precision
+    serving_stats = None
+    if a.serving_requests > 0 and rank == 0:
+        from paper_2505_20375_gb300 import serving
+
+        reqs = serving.make_requests(a.serving_requests, rate=a.serving_rate, seed=5)
+        res, serving_stats = serving.Server(device=local_rank, max_active=16).run(reqs)
+        serving_stats["request_mix"] = "uniform over FCI(6e,6o),(8e,8o),(10e,10o),(12e,12o), DAS 4x4 orbitals 4a4b <=1 transfer"
+        serving_stats["rate_per_s"] = a.serving_rate
+        serving_stats["metric"] = "time from arrival to converged energy (|dE| <= 1e-9, ||r|| <= 1e-5)"
+        mixed = [r.latency for r in res if r.mixed]
+        plain = [r.latency for r in res if not r.mixed]
+        serving_stats["p50_mixed_s"] = float(np.percentile(mixed, 50)) if mixed else None
+        serving_stats["p50_fp64_s"] = float(np.percentile(plain, 50)) if plain else None
+
     # max over ranks
     if world > 1:
         t = torch.tensor([T, T_e2e], dtype=torch.float64, device=dev)
@@ -322,6 +341,7 @@ def run_ours(a, rank, world, local_rank):
         "cpu_baseline": cpu,
         "variants": variants,
         "davidson": davidson,
+        "serving": serving_stats,
         "fp64_peak_tflops_measured": fp64_peak,
     }
     return line
