@@ -46,6 +46,7 @@ def _args():
     ap.add_argument("--serving-requests", type=int, default=32,
                     help="requests of the serving run (0 = skip); 256 is the full request stream")
     ap.add_argument("--serving-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--no-configs", action="store_true", help="skip the single-sigma runs of the other configs")
     return ap.parse_args()
 
 
@@ -129,6 +130,25 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _build_fci(fci, synth, name):
+    w = synth.WORKLOADS[name]
+    h, g = synth.real_integrals(w["n"], w["n_chol"], w["seed"])
+    return fci.FCI(0).setup_integrals(h, g).build_strings(w["na"], w["nb"])
+
+
+def _build_das(fci, synth, name, nel):
+    w = synth.WORKLOADS[name]
+    h, g = synth.real_integrals(w["n"], w["n_chol"], w["seed"])
+    f = fci.FCI(0).setup_integrals(h, g).build_strings(nel, nel)
+    return f.build_das(w["spaces"], w["ref"], w["ref"], w["max_transfer"])
+
+
+def _build_spinor(fci, synth):
+    w = synth.WORKLOADS["spinor_24s12e"]
+    h, g = synth.complex_integrals(w["n"], w["n_chol"], w["seed"])
+    return fci.FCI(0).setup_integrals(h, g).build_strings(w["ne"], -1)
 
 
 # ------------------------------------------------------------------ our arm
@@ -269,6 +289,52 @@ def run_ours(a, rank, world, local_rank):
                 d["energy_error_vs_fp64"] = abs(d["energy"] - e64)
                 d["speedup_vs_fp64"] = davidson["fp64"]["seconds"] / d["seconds"]
 
+    # one sigma of each other configuration (parity-tested layouts), FP64 and split
+    config_runs = None
+    if not a.no_configs and rank == 0:
+        config_runs = {}
+        del flush
+        torch.cuda.empty_cache()
+        for name, build, precs in (
+                ("fci_8e8o", lambda: _build_fci(fci, synth, "fci_8e8o"), ("fp64", ("oz_bf16", 6))),
+                ("das_16o_4x4_16e_t2", lambda: _build_das(fci, synth, "das_16o_4x4", 8), ("fp64",)),
+                ("das_16o_4x4_8e_t1", lambda: _build_das(fci, synth, "das_16o_4x4_8e", 4), ("fp64",)),
+                ("spinor_24s12e", lambda: _build_spinor(fci, synth), ("fp64",))):
+            try:
+                g = build()
+                Nn = g.n_det
+                cx = torch.from_numpy(synth.random_vector(Nn, seed=7, complex_=g.is_complex)).to(dev)
+                row = {"n_det": Nn, "n_det_intermediate": g.info["n_det_intermediate"], "n_pair": g.info["n_pair"]}
+                for pr in precs:
+                    pname, sl = (pr, 0) if isinstance(pr, str) else pr
+                    o = g.sigma(cx, precision=pname, n_slices=sl)  # warm-up, workspace
+                    torch.cuda.synchronize()
+                    g.set_phase_timing(True)
+                    g.phase_times(reset=True)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    g.sigma(cx, precision=pname, n_slices=sl, out=o)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ph = g.phase_times(reset=True)
+                    g.set_phase_timing(False)
+                    ms = e0.elapsed_time(e1)
+                    key = pname if pname == "fp64" else f"{pname}_s{sl}"
+                    cms = ph["contract"]["ms"]
+                    m_rows = row["n_pair"]
+                    flops = (8.0 if g.is_complex else 2.0) * m_rows * m_rows * row["n_det_intermediate"]
+                    row[key] = {"ms": ms, "det_sigma_per_s": Nn / (ms * 1e-3),
+                                "phases_ms": {k: v["ms"] for k, v in ph.items()},
+                                "contract_tflops": flops / (cms * 1e-3) / 1e12 if cms > 0 and pname == "fp64" else None,
+                                "contract_frac_of_fp64_peak": (flops / (cms * 1e-3) / 1e12 / fp64_peak)
+                                if (cms > 0 and pname == "fp64" and fp64_peak) else None}
+                config_runs[name] = row
+                g.close()
+                del cx, o
+                torch.cuda.empty_cache()
+            except Exception as e:  # report, do not abort the benchmark
+                config_runs[name] = {"unavailable": str(e)[:200]}
+
     # continuous-batching serving: a Poisson stream of Davidson requests (FCI (6e,6o) ..
     # (12e,12o) and 16-orbital 4-space DAS), half of them in mixed precision
     serving_stats = None
@@ -342,6 +408,7 @@ def run_ours(a, rank, world, local_rank):
         "variants": variants,
         "davidson": davidson,
         "serving": serving_stats,
+        "configs": config_runs,
         "fp64_peak_tflops_measured": fp64_peak,
     }
     return line
