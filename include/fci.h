@@ -148,8 +148,11 @@ int fci_sigma_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slic
 /* sigma = H C for n_vec vectors (Methods, Eqs. sigmaL, sigmaL1e, sigmaL2e).
  *   C, sigma: DEVICE pointers, n_vec x info.n_det, vector-major, double (R64) or
  *             interleaved complex (C128); must not overlap;
- *   precision: FCI_PREC_FP64, or FCI_PREC_OZ_BF16 with n_slices in [2, 8] bf16 slices
- *             of each operand of the contraction (R64 only);
+ *   precision: FCI_PREC_FP64, or FCI_PREC_OZ_BF16 with n_slices 16-bit digit slices of
+ *             each operand of the contraction (R64 only): alpha/beta strings take 2..7
+ *             slices (n_orb <= 15; 6 and 7 reach the FP64 tolerance); the DAS layout
+ *             takes 2 or 3 slices (n_orb <= 17), with E stored in FP32, for the first
+ *             phase of a mixed-precision solve; FCI_ERR_UNSUPPORTED otherwise;
  *   workspace: DEVICE pointer, >= fci_sigma_workspace_bytes, 256-byte aligned.
  * Asynchronous on `stream`. */
 int fci_sigma(fci_handle h, const void *C, void *sigma, int n_vec, int precision,
@@ -237,10 +240,10 @@ typedef struct {
 } fci_sigma_job;
 
 /* sigma builds of several problems (different handles, sizes and integrals) in one pass
- * on `stream`: jobs that use FCI_PREC_OZ_BF16 on alpha/beta strings with the same slice
- * count share ONE persistent launch of the tcgen05 contraction kernel (the uneven tile
- * ranges of all jobs in one grid, CTAs split in proportion to each job's tiles); the other
- * jobs run one after another.  All handles must be on the same device; a handle may
+ * on `stream`: jobs that use FCI_PREC_OZ_BF16 with the same slice count share ONE
+ * persistent launch of the tcgen05 contraction kernel (the uneven tile ranges of all jobs
+ * in one grid, CTAs split in proportion to each job's tiles; alpha/beta-string jobs and
+ * DAS jobs form separate launches); the other jobs run one after another.  All handles must be on the same device; a handle may
  * appear in at most one job.  Asynchronous.  This is the batching the serving loop uses
  * for the sigma builds of concurrent Davidson solves (not a step of the paper's method). */
 int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream);

@@ -41,7 +41,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
+    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(HERE, "..", "include", "*.h"))
     flags = FLAGS + list(extra_flags or [])
     jobs = []
     objs = []

@@ -169,6 +169,7 @@ void das_free(fci_context *h) {
                     L.d_cat_pa, L.d_cat_pb, L.d_cat_off, L.d_str_of_loc_a, L.d_str_of_loc_b,
                     L.d_pat_locbase_a, L.d_pat_locbase_b};
     for (void *p : ptrs) fci_dev_free(p);
+    dz_free(L);
     L = fci_das_layout();
     h->das_active = false;
     if (h->mode == FCI_MODE_DAS) h->mode = FCI_MODE_FCI;
@@ -335,8 +336,7 @@ static int64_t das_chunk_len(const fci_context *h) {
 }
 
 size_t das_workspace_bytes(const fci_context *h, int precision, int n_slices) {
-    (void)precision;
-    (void)n_slices;
+    if (precision == FCI_PREC_OZ_BF16) return dz_workspace_bytes(h, n_slices);
     const int64_t len = das_chunk_len(h);
     return 2 * al((size_t)h->npair * len * 8);
 }
@@ -375,8 +375,9 @@ int das_sigma_fp64(fci_context *h, const double *C, double *sigma, void *ws, siz
     return FCI_OK;
 }
 
-int das_sigma_oz(fci_context *h, const double *, double *, int, void *, size_t, cudaStream_t) {
-    return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is not built for the DAS layout; use FCI_PREC_FP64");
+int das_sigma_oz(fci_context *h, const double *C, double *sigma, int n_slices, void *ws, size_t ws_bytes,
+                 cudaStream_t s) {
+    return dz_sigma(h, C, sigma, n_slices, ws, ws_bytes, s);
 }
 
 cudaError_t launch_diag_das(const fci_context *h, double *diag, cudaStream_t s) {

@@ -513,6 +513,14 @@ static int check_opts(fci_context *h, const fci_davidson_opts *o) {
         return fci_fail(h, FCI_ERR_ARG, "unknown final precision %d", o->final_precision);
     if (o->final_precision == FCI_PREC_OZ_BF16 && (o->final_slices < 6 || o->final_slices > 8))
         return fci_fail(h, FCI_ERR_ARG, "final_slices %d outside [6, 8]", o->final_slices);
+    if (h->das_active) {  // the DAS split path takes 2 or 3 slices; its FP64-class phase is FP64
+        if (o->precision == FCI_PREC_OZ_BF16) {
+            const int rc = dz_check(h, o->n_slices);
+            if (rc) return rc;
+        }
+        if (o->final_precision == FCI_PREC_OZ_BF16)
+            return fci_fail(h, FCI_ERR_UNSUPPORTED, "DAS layout: the final phase runs in FCI_PREC_FP64");
+    }
     return FCI_OK;
 }
 
@@ -634,6 +642,27 @@ int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream) 
             done[k] = 1;
         }
         int rc = oz_sigma_group(hs.data(), Cs.data(), ss.data(), ws.data(), (int)hs.size(), j.n_slices, s);
+        if (rc) return rc;
+    }
+    // split-precision DAS jobs, grouped by slice count
+    for (int i = 0; i < n_jobs; ++i) {
+        const fci_sigma_job &j = jobs[i];
+        if (done[i] || j.precision != FCI_PREC_OZ_BF16 || !j.handle->das_active) continue;
+        std::vector<fci_context *> hs;
+        std::vector<const double *> Cs;
+        std::vector<double *> ss;
+        std::vector<void *> ws;
+        for (int k = i; k < n_jobs; ++k) {
+            const fci_sigma_job &q = jobs[k];
+            if (done[k] || q.precision != FCI_PREC_OZ_BF16 || q.n_slices != j.n_slices || !q.handle->das_active)
+                continue;
+            hs.push_back(q.handle);
+            Cs.push_back((const double *)q.C);
+            ss.push_back((double *)q.sigma);
+            ws.push_back(q.workspace);
+            done[k] = 1;
+        }
+        int rc = dz_sigma_group(hs.data(), Cs.data(), ss.data(), ws.data(), (int)hs.size(), j.n_slices, s);
         if (rc) return rc;
     }
     for (int i = 0; i < n_jobs; ++i) {

@@ -59,6 +59,15 @@ struct fci_das_layout {
     int32_t *d_str_of_loc_a = nullptr;      // [n_pat_a][max local] -> global alpha index
     int32_t *d_str_of_loc_b = nullptr;
     int64_t *d_pat_locbase_a = nullptr, *d_pat_locbase_b = nullptr;  // offsets into str_of_loc
+    // split-precision operands (built on first use): replacement tables that pack the
+    // target string's pattern and local index, block offsets per pattern pair, and the
+    // G digit slices in the layout of the MMA's B operand
+    int32_t *d_dz_rep_a = nullptr, *d_dz_rep_b = nullptr;  // [n_pair_pad][n_str]
+    int32_t *d_dz_base = nullptr;  // [target | intermediate block offset per pattern pair (-1: none) | n_str_b]
+    void *d_dz_G = nullptr;
+    int dz_slices = 0, dz_shG = 0;
+    // kernel configuration chosen by the tuner for dz_tuned_slices (0: none)
+    int dz_tuned_slices = 0, dz_tuned_kch = 0, dz_tuned_pw = 0;
 };
 
 struct fci_context {
@@ -185,6 +194,15 @@ int das_sigma_oz(fci_context *h, const double *C, double *sigma, int n_slices, v
 size_t das_workspace_bytes(const fci_context *h, int precision, int n_slices);
 cudaError_t launch_diag_das(const fci_context *h, double *diag, cudaStream_t s);
 cudaError_t launch_das_export_address(const fci_context *h, int64_t *dst, cudaStream_t s);
+
+// ozaki_das.cu
+size_t dz_workspace_bytes(const fci_context *h, int n_slices);
+int dz_sigma(fci_context *h, const double *C, double *sigma, int n_slices, void *ws, size_t ws_bytes,
+             cudaStream_t s);
+int dz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
+                   int s, cudaStream_t st);
+void dz_free(fci_das_layout &L);
+int dz_check(fci_context *h, int n_slices);  // FCI_OK if the DAS split path takes this problem
 
 // ozaki.cu
 int oz_prepare_G(fci_context *h, int n_slices);

@@ -1,0 +1,1052 @@
+// Split-precision sigma on the STP-DAS layout (Results: the CI vector as category
+// blocks; Methods, Eqs. sigmaL1e/sigmaL2e: the sigma build as gather, dense
+// contraction E = g' D and scatter), with the contraction on the tcgen05 tensor cores,
+// Ozaki style.
+//
+// Same scheme as the alpha/beta kernel: both operands go to fixed point with one
+// exponent each, are cut into s signed base-256 digits (exact in f16), and the level
+// sums S_L = sum_{i+j=L} G_i D_j of the top s levels (L >= s - 1) accumulate exactly in
+// FP32 TMEM columns.  The MMA operands are turned around to fit the DAS sizes (16 and
+// 17 orbitals have 136 and 153 pair rows, more than one M = 128 tile):
+//   M = 128 determinants of the intermediate space per tile (A operand: digit planes
+//       of D^T, produced K-chunk by K-chunk into a shared-memory ring),
+//   N = n_pair rounded up to 16 (B operand: the G digit slices, resident in shared
+//       memory), K = the same padded n_pair.
+// s = 2 or 3 slices: s level accumulators of N columns each fit the 512 TMEM columns.
+// At these s every |C_int| < 2^21, so C goes to int32 fixed point; the exact level
+// combination E_int (|E_int| < 2^40) is stored rounded to FP32 (24 significant bits,
+// far below the 2^-8s truncation of the split), and the scatter turns each stored value
+// back into the integer it holds and sums in int64:
+//   sigma_I = 2^{8(s-1) - sh_G - sh_C} sum <I|E_pq|K> E[pq, K] + e_core C_I.
+// E spans the intermediate space (target plus one-more-transfer categories) in chunks
+// of whole categories that fit the workspace.  Addressing: a per-string replacement
+// table packs the target string's pattern and local index with the sign, so the
+// address of a connected determinant is a table lookup, one block offset per
+// (alpha pattern, beta pattern) held in shared memory, and a multiply-add.
+//
+// Kernel layout (one persistent CTA per SM, 544 threads):
+//   warps 0-7   producers: decode the tile's determinants (category, strings, local
+//               indices) once per tile, then per K-chunk gather D_int for 128
+//               determinants x 8 KCH pairs from C_int and write its s digit planes;
+//   warps 8-15  epilogue: per TMEM lane quadrant two warps split the N columns, read the
+//               s levels in chunks of 16, combine in int64, store E (FP32, pair-major
+//               inside each tile of 128 determinants);
+//   warp 16     allocates TMEM; lane 0 issues the MMAs and the commits.
+// Tiles are dealt round-robin to the CTAs of a job, so at any time the CTAs work on
+// neighbouring determinants and share the rows of C they gather (L2 locality).
+// Waits on mbarriers are bounded in time as in the alpha/beta kernel.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "das_dev.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+using namespace tc;
+using das_dev::find_cat;
+
+constexpr int DZ_TILE = 128;  // determinants per tile (the MMA's M)
+constexpr int DZ_EPILOGUE_WARPS = 4;  // one per TMEM lane quadrant
+__host__ __device__ constexpr int dz_threads(int pw) { return 32 * (pw + DZ_EPILOGUE_WARPS + 1); }
+constexpr int DZ_MAX_RING = 4;
+constexpr int DZ_LOC_BITS = 22;  // packed replacement entry: ((pattern << 22 | local) << 1) | sign
+constexpr int32_t DZ_LOC_MASK = (1 << DZ_LOC_BITS) - 1;
+constexpr int DZ_MAX_JOBS = 16;
+constexpr size_t DZ_SMEM_MAX = 232448 - 1024;  // dynamic shared memory (static: the job parameters)
+
+struct DzParams {
+    int64_t a0, len;  // this launch covers intermediate addresses [a0, a0 + len)
+    int64_t n_det;    // target determinants (C is zero beyond)
+    int64_t nla, nlb; // strings of the listed patterns (the rows of the replacement tables)
+    int n_cat_int;    // categories searched when decoding an address
+    int n_pat_a, n_pat_b;
+    int npair, Np, KC, ring;
+    int g_slice_bytes, slot_bytes, tab_off;  // shared-memory layout
+    const int32_t *repA, *repB;
+    const int32_t *base_tgt;  // [n_pat_a * n_pat_b]: offset of a TARGET block, else -1 (C is zero)
+    const int32_t *nstr_b32;  // [n_pat_b]
+    const int64_t *cat_off;
+    const int32_t *cat_pa, *cat_pb;
+    const int64_t *locbase_a, *locbase_b;
+    const int32_t *Cint;
+    const uint4 *Gimg;
+    float *E;
+    int *status;
+    long long timeout_cycles;
+};
+
+struct DzGroup {
+    int n_jobs;
+    int cta_start[DZ_MAX_JOBS + 1];
+    DzParams job[DZ_MAX_JOBS];
+};
+
+struct DzShared {
+    uint64_t plane_full[DZ_MAX_RING], plane_empty[DZ_MAX_RING];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ bool dz_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                        long long timeout) {
+    const long long t0 = clock64();
+    int spins = 0;
+    while (!mbar_try_wait_sleep(bar, parity)) {
+        if (((++spins) & 3) == 0) {
+            if (*abort) return false;
+            if (clock64() - t0 > timeout) {
+                *abort = 1;
+                atomicExch(status, FCI_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool dz_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                             long long timeout) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = dz_wait(bar, parity, abort, status, timeout) ? 1 : 0;
+    return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
+}
+
+// S: slices per operand; KCH: K-cores (8 pairs each) per ring slot, 2, 4 or 6;
+// PW: producer warps (8 or 12; KCH a multiple of PW / 4).  Warps PW .. PW+3 run the
+// epilogue, warp PW+4 the MMAs.
+template <int S, int KCH, int PW>
+__global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_constant__ DzGroup grp) {
+    __shared__ DzParams p;
+    __shared__ int cta_lo, cta_n;
+    if (threadIdx.x == 0) {
+        int jb = 0;
+        while (jb + 1 < grp.n_jobs && (int)blockIdx.x >= grp.cta_start[jb + 1]) ++jb;
+        p = grp.job[jb];
+        cta_lo = grp.cta_start[jb];
+        cta_n = grp.cta_start[jb + 1] - grp.cta_start[jb];
+    }
+    __syncthreads();
+    constexpr int HG = PW / 4;            // producer threads per determinant
+    constexpr int UNITS = KCH / HG;       // K-cores per producer thread per chunk
+    constexpr int EW = DZ_EPILOGUE_WARPS;
+    constexpr int DZ_MMA_WARP = PW + EW;
+    static_assert(KCH % HG == 0, "K-chunk not divisible among the producer threads");
+    extern __shared__ __align__(1024) uint8_t dz_smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)dz_smem_raw + 1023) & ~(uintptr_t)1023);
+    const int Np = p.Np, KC = p.KC, RING = p.ring;
+    const int nbuf = (2 * S * Np <= 512) ? 2 : 1;
+    const int plane_bytes = DZ_TILE * KCH * 16;
+    uint8_t *sG = smem;
+    uint8_t *sRing = sG + (size_t)S * p.g_slice_bytes;
+    const int npab = p.n_pat_a * p.n_pat_b;
+    int32_t *sBase = (int32_t *)(smem + p.tab_off);  // [n_pat_a * n_pat_b] target block offsets
+    int32_t *sNstrB = sBase + npab;                  // [n_pat_b]
+    int32_t *sRowAll = sNstrB + p.n_pat_b;           // [PW][n_pat_b]: per-warp row offsets
+    DzShared *sh = (DzShared *)(((uintptr_t)(sRowAll + PW * p.n_pat_b) + 15) & ~(uintptr_t)15);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    {
+        const int n16 = S * p.g_slice_bytes / 16;
+        uint4 *dst = (uint4 *)sG;
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(p.Gimg + i);
+        for (int i = threadIdx.x; i < npab; i += blockDim.x) sBase[i] = __ldg(p.base_tgt + i);
+        for (int i = threadIdx.x; i < p.n_pat_b; i += blockDim.x) sNstrB[i] = __ldg(p.nstr_b32 + i);
+    }
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < RING; ++r) {
+            mbar_init(smem_u32(&sh->plane_full[r]), PW);
+            mbar_init(smem_u32(&sh->plane_empty[r]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&sh->acc_full[b]), 1);
+            mbar_init(smem_u32(&sh->acc_empty[b]), EW);
+        }
+        mbar_init(smem_u32(&sh->drain), 1);
+        sh->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == DZ_MMA_WARP) {
+        tmem_alloc(smem_u32(&sh->tmem_base), 512);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort = &sh->abort;
+    const int64_t ntiles = (p.len + DZ_TILE - 1) / DZ_TILE;
+    const int64_t cta = (int64_t)blockIdx.x - cta_lo;
+    const int nch = KC / KCH;
+
+    if (warp < PW) {
+        // ---------------------------------------------------------------- producers
+        // Thread t: determinant r = t % 128 of the tile, K-cores hg, hg + HG, ... of each
+        // chunk (hg = t / 128); a warp covers 32 consecutive determinants.  Replacement
+        // tables are indexed by the pattern-local string (beta entries of a warp are
+        // consecutive); block offsets are -1 where C is zero (non-target categories).
+        // Common case, a warp whose determinants share the alpha string (one row of a
+        // block): lanes 0-7 look up the alpha moves of the unit's 8 pairs once and
+        // broadcast them (alpha targets are then 32 consecutive C values), and beta
+        // targets go through a per-warp table of row offsets for that alpha string.
+        // Otherwise every lane resolves its own moves.  Pair-table rows beyond n_pair
+        // hold -1; all loads of a unit are issued before any is used.
+        const int t = threadIdx.x;
+        const int r = t & (DZ_TILE - 1), hg = t >> 7;
+        constexpr uint32_t bias = S == 3 ? 0x808080u : 0x8080u;
+        const int npb = p.n_pat_b;
+        int32_t *sRow = sRowAll + warp * npb;
+        const int32_t nla = (int32_t)p.nla, nlb = (int32_t)p.nlb;
+        uint32_t q = 0;
+        for (int64_t tile = cta; tile < ntiles; tile += cta_n) {
+            const int64_t off = tile * DZ_TILE + r;
+            const bool live = off < p.len;
+            int32_t pa = 0, pb = 0, la = 0, lb = 0, ida = 0, idb = 0, nb = 1;
+            if (live) {
+                const int64_t addr = p.a0 + off;
+                const int c = find_cat(p.cat_off, p.n_cat_int, addr);
+                pa = __ldg(p.cat_pa + c);
+                pb = __ldg(p.cat_pb + c);
+                nb = sNstrB[pb];
+                const int32_t rr = (int32_t)(addr - __ldg(p.cat_off + c));
+                la = rr / nb;
+                lb = rr - la * nb;
+                ida = (int32_t)__ldg(p.locbase_a + pa) + la;
+                idb = (int32_t)__ldg(p.locbase_b + pb) + lb;
+            }
+            // one alpha string across the warp?  (lanes past the end agree trivially)
+            const int pa0 = __shfl_sync(0xFFFFFFFFu, pa, 0), la0 = __shfl_sync(0xFFFFFFFFu, la, 0);
+            const int pb0 = __shfl_sync(0xFFFFFFFFu, pb, 0), nb0 = __shfl_sync(0xFFFFFFFFu, nb, 0);
+            const int32_t ida0 = __shfl_sync(0xFFFFFFFFu, ida, 0);
+            const bool live0 = __shfl_sync(0xFFFFFFFFu, live ? 1 : 0, 0) != 0;  // false: no lane is live
+            const bool uni = __all_sync(0xFFFFFFFFu, !live || (pa == pa0 && la == la0 && pb == pb0));
+            if (uni) {
+                __syncwarp();  // every lane is done with the previous tile's table
+                for (int k = lane; k < npb; k += 32) {
+                    const int32_t b = sBase[pa0 * npb + k];
+                    sRow[k] = b >= 0 ? b + la0 * sNstrB[k] : -1;
+                }
+                __syncwarp();
+            }
+            const int32_t *bA = sBase + pb;  // alpha moves: [pa' * npb + pb]
+            const int32_t *bB = sBase + pa * npb;  // beta moves: [pa * npb + pb']
+            for (int ch = 0; ch < nch; ++ch, ++q) {
+                uint32_t y[UNITS][8];
+#pragma unroll
+                for (int u = 0; u < UNITS; ++u) {
+                    const int gc = ch * KCH + hg + HG * u;
+                    int32_t Ka[8], Kb[8];
+                    uint32_t sgn = 0;  // bit e: alpha sign, bit 8 + e: beta sign
+                    if (uni) {
+                        // lane e < 8 resolves the alpha move of pair 8 gc + e for the warp's
+                        // alpha string (lane 0's), as (target row offset << 1) | sign
+                        int32_t ab = -1;
+                        if (lane < 8 && live0) {
+                            const int32_t ea = __ldg(p.repA + (8 * gc + lane) * nla + ida0);
+                            if (ea >= 0) {
+                                const int32_t b = sBase[(ea >> 23) * npb + pb0];
+                                ab = b >= 0 ? ((b + ((ea >> 1) & DZ_LOC_MASK) * nb0) << 1) | (ea & 1) : -1;
+                            }
+                        }
+                        int32_t eb[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) eb[e] = live ? __ldg(p.repB + (8 * gc + e) * nlb + idb) : -1;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int32_t a = __shfl_sync(0xFFFFFFFFu, ab, e);
+                            Ka[e] = (a >= 0 && live) ? (a >> 1) + lb : -1;
+                            sgn |= (uint32_t)(a & 1) << e;
+                            const int32_t rb = eb[e] >= 0 ? sRow[eb[e] >> 23] : -1;
+                            Kb[e] = rb >= 0 ? rb + ((eb[e] >> 1) & DZ_LOC_MASK) : -1;
+                            sgn |= (uint32_t)(eb[e] & 1) << (8 + e);
+                        }
+                    } else {
+                        int32_t ea[8], eb[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            ea[e] = live ? __ldg(p.repA + (8 * gc + e) * nla + ida) : -1;
+                            eb[e] = live ? __ldg(p.repB + (8 * gc + e) * nlb + idb) : -1;
+                        }
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int32_t ba = ea[e] >= 0 ? bA[(ea[e] >> 23) * npb] : -1;
+                            const int32_t bb = eb[e] >= 0 ? bB[eb[e] >> 23] : -1;
+                            Ka[e] = ba >= 0 ? ba + ((ea[e] >> 1) & DZ_LOC_MASK) * nb + lb : -1;
+                            Kb[e] = bb >= 0 ? bb + la * sNstrB[eb[e] >> 23] + ((eb[e] >> 1) & DZ_LOC_MASK) : -1;
+                            sgn |= ((uint32_t)(ea[e] & 1) << e) | ((uint32_t)(eb[e] & 1) << (8 + e));
+                        }
+                    }
+                    int32_t xa[8], xb[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        xa[e] = __ldg(p.Cint + (Ka[e] < 0 ? 0 : Ka[e]));
+                        xb[e] = __ldg(p.Cint + (Kb[e] < 0 ? 0 : Kb[e]));
+                    }
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        const int32_t va = Ka[e] < 0 ? 0 : (((sgn >> e) & 1) ? -xa[e] : xa[e]);
+                        const int32_t vb = Kb[e] < 0 ? 0 : (((sgn >> (8 + e)) & 1) ? -xb[e] : xb[e]);
+                        y[u][e] = (uint32_t)(va + vb) + bias;
+                    }
+                }
+                const int slot = (int)(q % (uint32_t)RING);
+                const uint32_t use = q / (uint32_t)RING;
+                if (use > 0 && !dz_wait_warp(smem_u32(&sh->plane_empty[slot]), (use - 1) & 1, abort, p.status,
+                                             p.timeout_cycles))
+                    goto producer_done;
+                {
+                    uint8_t *sl = sRing + (size_t)slot * p.slot_bytes;
+#pragma unroll
+                    for (int j = 0; j < S; ++j) {
+                        const uint32_t sel = (uint32_t)j | ((4u + (uint32_t)j) << 8);
+#pragma unroll
+                        for (int u = 0; u < UNITS; ++u) {
+                            const int c = hg + HG * u;
+                            uint32_t w[4];
+#pragma unroll
+                            for (int e = 0; e < 8; e += 2) w[e / 2] = digits_f16x2(y[u][e], y[u][e + 1], sel);
+                            const uint32_t o = (uint32_t)(((r >> 3) * KCH + c) * 128 + (r & 7) * 16);
+                            *(uint4 *)(sl + j * plane_bytes + o) = make_uint4(w[0], w[1], w[2], w[3]);
+                        }
+                    }
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->plane_full[slot]));
+            }
+        }
+    producer_done:;
+    } else if (warp < DZ_MMA_WARP) {
+        // ---------------------------------------------------------------- epilogue
+        const int ew = warp - PW;
+        const int qd = warp & 3;  // the TMEM lane quadrant this warp may access
+        (void)ew;
+        const int nck = Np / 16;
+        const int row = 32 * qd + lane;  // determinant within the tile
+        uint32_t tau = 0;
+        for (int64_t tile = cta; tile < ntiles; tile += cta_n, ++tau) {
+            const int buf = nbuf == 2 ? (int)(tau & 1) : 0;
+            const uint32_t par = nbuf == 2 ? (tau >> 1) & 1 : tau & 1;
+            if (!dz_wait_warp(smem_u32(&sh->acc_full[buf]), par, abort, p.status, p.timeout_cycles)) break;
+            tc_fence_after();
+            const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * Np);
+            float *Et = p.E + tile * ((int64_t)p.npair * DZ_TILE) + row;
+#pragma unroll 1
+            for (int ck = 0; ck < nck; ++ck) {
+                int64_t acc[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[c] = 0;
+#pragma unroll
+                for (int l = 0; l < S; ++l) {
+                    uint32_t v[16];
+                    tmem_ld16(tl + (uint32_t)(l * Np + 16 * ck), v);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * l));
+                }
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int pp = 16 * ck + c;
+                    if (pp < p.npair) __stcs(Et + (int64_t)pp * DZ_TILE, __ll2float_rn(acc[c]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
+        }
+    } else if (lane == 0) {
+        // ---------------------------------------------------------------- MMA issuer
+        const uint32_t idesc = idesc_f16(DZ_TILE, Np);
+        uint64_t bdesc[S];
+#pragma unroll
+        for (int i = 0; i < S; ++i)
+            bdesc[i] = smem_desc(smem_u32(sG) + (uint32_t)(i * p.g_slice_bytes), 128, (uint32_t)(KC * 128));
+        const uint64_t adesc0 = smem_desc(smem_u32(sRing), 128, (uint32_t)(KCH * 128));
+        const uint32_t slot_step = (uint32_t)(p.slot_bytes >> 4), plane_step = (uint32_t)(plane_bytes >> 4);
+        uint32_t q = 0, tau = 0;
+        bool issued = false;
+        for (int64_t tile = cta; tile < ntiles; tile += cta_n, ++tau) {
+            const int buf = nbuf == 2 ? (int)(tau & 1) : 0;
+            if (tau >= (uint32_t)nbuf) {
+                const uint32_t par = nbuf == 2 ? ((tau >> 1) - 1) & 1 : (tau - 1) & 1;
+                if (!dz_wait(smem_u32(&sh->acc_empty[buf]), par, abort, p.status, p.timeout_cycles)) break;
+            }
+            tc_fence_after();
+            const uint32_t dbase = tmem + (uint32_t)(buf * S * Np);
+            bool ok = true;
+            for (int ch = 0; ch < nch; ++ch, ++q) {
+                const int slot = (int)(q % (uint32_t)RING);
+                if (!dz_wait(smem_u32(&sh->plane_full[slot]), (q / (uint32_t)RING) & 1, abort, p.status,
+                             p.timeout_cycles)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t a0 = adesc0 + (uint64_t)(slot * slot_step);
+#pragma unroll
+                for (int kk = 0; kk < KCH / 2; ++kk) {
+                    const uint32_t koff = (uint32_t)((ch * (KCH / 2) + kk) * 16);
+#pragma unroll
+                    for (int j = S - 1; j >= 0; --j) {
+                        const uint64_t a = a0 + (uint64_t)(j * plane_step + kk * 16);
+                        const uint32_t acc_in = (ch != 0 || kk != 0 || j != S - 1) ? 1u : 0u;
+#pragma unroll
+                        for (int i = S - 1 - j; i < S; ++i)
+                            mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * Np), a, bdesc[i] + koff, idesc, acc_in);
+                    }
+                }
+                issued = true;
+                mma_commit(smem_u32(&sh->plane_empty[slot]));
+            }
+            if (!ok) break;
+            mma_commit(smem_u32(&sh->acc_full[buf]));
+        }
+        if (issued) {
+            mma_commit(smem_u32(&sh->drain));
+            const long long t0 = clock64();
+            while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
+                if (clock64() - t0 > p.timeout_cycles) {
+                    atomicExch(p.status, FCI_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == DZ_MMA_WARP) tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------- helper kernels
+
+// Packed replacement table of one spin, rows = pair index, columns = the strings of the
+// listed patterns in pattern-local order (pattern by pattern, local index ascending):
+// entry (pair row, string) of the alpha/beta pair table, (target << 1) | sign, becomes
+// ((pattern(target) << 22 | local(target)) << 1) | sign, or -1 when there is no
+// replacement or the target's pattern is outside the layout (more than max_transfer + 1
+// electrons moved).
+__global__ void k_dz_rep(const int32_t *__restrict__ pairtab, int64_t ns, int rows,
+                         const int32_t *__restrict__ str_of_loc, int64_t nl, const int32_t *__restrict__ pat_of,
+                         const int32_t *__restrict__ loc_of, int32_t *__restrict__ out) {
+    const int64_t n = (int64_t)rows * nl;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / nl, col = i - row * nl;
+        const int32_t e = pairtab[row * ns + str_of_loc[col]];
+        int32_t o = -1;
+        if (e >= 0) {
+            const int32_t T = e >> 1, pt = pat_of[T];
+            if (pt >= 0) o = (((pt << DZ_LOC_BITS) | loc_of[T]) << 1) | (e & 1);
+        }
+        out[i] = o;
+    }
+}
+
+__global__ void k_dz_absmax(const double *__restrict__ x, int64_t n, unsigned long long *__restrict__ out) {
+    unsigned long long m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(x[i]) & 0x7FFFFFFFFFFFFFFFull);
+    for (int o = 16; o; o >>= 1) m = max(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+// C_int = round(C 2^{sh_C}), sh_C = 8 s - 3 - e_C with max|C| < 2^{e_C}: |C_int| < 2^{8s-3}
+// (< 2^21 for s <= 3, so int32 holds it).
+__global__ void k_dz_to_fixed(const double *__restrict__ C, int64_t n, int s,
+                              const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ Cint,
+                              int *__restrict__ shC) {
+    const unsigned long long mb = *maxbits;
+    const int e = mb ? (int)((mb >> 52) & 0x7FF) - 1022 : 0;
+    const int sh = 8 * s - 3 - e;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *shC = sh;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        Cint[i] = (int32_t)__double2ll_rn(scalbn(C[i], sh));
+}
+
+struct DzScatter {
+    int64_t n_det, a0, len;
+    int nla, nlb;
+    int n_cat, n_pat_a, n_pat_b, npair;
+    const int32_t *repA, *repB;
+    const int32_t *base_int;  // [n_pat_a * n_pat_b]: offset of a block of the intermediate space, else -1
+    const int32_t *nstr_b32;
+    const int64_t *cat_off, *locbase_a, *locbase_b;
+    const int32_t *cat_pa, *cat_pb;
+    const float *E;
+    const double *C;
+    double e_core;
+    int ushift;  // 8 (s - 1) - sh_G; the scale is 2^(ushift - sh_C)
+    const int *shC, *status;
+    int mode;    // 0: single chunk (write sigma); 1: first of several; 2: middle; 3: last
+    int64_t *acc;
+    double *sigma;
+};
+
+// sigma_I for every target determinant: sum of <I|E_pq|K> E[pq, K] over the K of this
+// chunk, in int64 (exact), then one conversion.  A warp takes 32 consecutive target
+// determinants; when they share the alpha string, lanes 0-7 resolve the alpha moves of 8
+// pairs at a time and broadcast them (alpha targets are 32 consecutive K), and beta
+// targets use a per-warp table of row offsets.  Loads are issued 16 at a time.
+__global__ void __launch_bounds__(256) k_dz_scatter(const __grid_constant__ DzScatter a) {
+    extern __shared__ int32_t sc_tab[];
+    const int npb = a.n_pat_b, npab = a.n_pat_a * npb;
+    int32_t *cb = sc_tab, *nst = sc_tab + npab, *rowAll = nst + npb;
+    for (int i = threadIdx.x; i < npab; i += blockDim.x) cb[i] = __ldg(a.base_int + i);
+    for (int i = threadIdx.x; i < npb; i += blockDim.x) nst[i] = __ldg(a.nstr_b32 + i);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    int32_t *row = rowAll + (threadIdx.x >> 5) * npb;
+    const int u = a.ushift - *a.shC;
+    const bool bad = *a.status != 0;
+    const int64_t tstride = (int64_t)a.npair * DZ_TILE;
+    const int32_t len = (int32_t)a.len, a0 = (int32_t)a.a0;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t wbase = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; wbase < a.n_det;
+         wbase += nwarps * 32) {
+        const int64_t I = wbase + lane;
+        const bool live = I < a.n_det;
+        int32_t pa = 0, pb = 0, la = 0, lb = 0, ida = 0, idb = 0, nb = 1;
+        if (live) {
+            const int c = find_cat(a.cat_off, a.n_cat, I);
+            pa = __ldg(a.cat_pa + c);
+            pb = __ldg(a.cat_pb + c);
+            nb = nst[pb];
+            const int32_t rr = (int32_t)(I - __ldg(a.cat_off + c));
+            la = rr / nb;
+            lb = rr - la * nb;
+            ida = (int32_t)__ldg(a.locbase_a + pa) + la;
+            idb = (int32_t)__ldg(a.locbase_b + pb) + lb;
+        }
+        const int pa0 = __shfl_sync(0xFFFFFFFFu, pa, 0), la0 = __shfl_sync(0xFFFFFFFFu, la, 0);
+        const int pb0 = __shfl_sync(0xFFFFFFFFu, pb, 0), nb0 = __shfl_sync(0xFFFFFFFFu, nb, 0);
+        const int32_t ida0 = __shfl_sync(0xFFFFFFFFu, ida, 0);
+        const bool uni = __all_sync(0xFFFFFFFFu, !live || (pa == pa0 && la == la0 && pb == pb0));
+        if (uni) {
+            __syncwarp();
+            for (int k = lane; k < npb; k += 32) {
+                const int32_t b = cb[pa0 * npb + k];
+                row[k] = b >= 0 ? b + la0 * nst[k] : -1;
+            }
+            __syncwarp();
+        }
+        int64_t acc = 0;
+        for (int p0 = 0; p0 < a.npair; p0 += 8) {  // pair-table rows beyond n_pair hold -1
+            int32_t Ka[8], Kb[8];
+            uint32_t sgn = 0;
+            if (uni) {
+                int32_t ab = INT32_MIN;  // (K - a0) * 2 + sign; the offset may be negative
+                if (lane < 8) {
+                    const int32_t ea = __ldg(a.repA + (p0 + lane) * a.nla + ida0);
+                    if (ea >= 0) {
+                        const int32_t b = cb[(ea >> 23) * npb + pb0];
+                        ab = b >= 0 ? ((b + ((ea >> 1) & DZ_LOC_MASK) * nb0 - a0) * 2) | (ea & 1) : INT32_MIN;
+                    }
+                }
+                int32_t eb[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) eb[e] = live ? __ldg(a.repB + (p0 + e) * a.nlb + idb) : -1;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int32_t x = __shfl_sync(0xFFFFFFFFu, ab, e);
+                    Ka[e] = x != INT32_MIN ? (x >> 1) + lb : -1;
+                    sgn |= (uint32_t)(x & 1) << e;
+                    const int32_t rb = eb[e] >= 0 ? row[eb[e] >> 23] : -1;
+                    Kb[e] = rb >= 0 ? rb + ((eb[e] >> 1) & DZ_LOC_MASK) - a0 : -1;
+                    sgn |= (uint32_t)(eb[e] & 1) << (8 + e);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int32_t ea = live ? __ldg(a.repA + (p0 + e) * a.nla + ida) : -1;
+                    const int32_t eb = live ? __ldg(a.repB + (p0 + e) * a.nlb + idb) : -1;
+                    const int32_t ba = ea >= 0 ? cb[(ea >> 23) * npb + pb] : -1;
+                    const int32_t bb = eb >= 0 ? cb[pa * npb + (eb >> 23)] : -1;
+                    Ka[e] = ba >= 0 ? ba + ((ea >> 1) & DZ_LOC_MASK) * nb + lb - a0 : -1;
+                    Kb[e] = bb >= 0 ? bb + la * nst[eb >> 23] + ((eb >> 1) & DZ_LOC_MASK) - a0 : -1;
+                    sgn |= ((uint32_t)(ea & 1) << e) | ((uint32_t)(eb & 1) << (8 + e));
+                }
+            }
+            float va[8], vb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const bool oa = live && Ka[e] >= 0 && Ka[e] < len, ob = Kb[e] >= 0 && Kb[e] < len;
+                const int32_t ka = oa ? Ka[e] : 0, kb = ob ? Kb[e] : 0;
+                va[e] = oa ? __ldg(a.E + (int64_t)(ka >> 7) * tstride + (p0 + e) * DZ_TILE + (ka & 127)) : 0.f;
+                vb[e] = ob ? __ldg(a.E + (int64_t)(kb >> 7) * tstride + (p0 + e) * DZ_TILE + (kb & 127)) : 0.f;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t xa = __float2ll_rn(va[e]), xb = __float2ll_rn(vb[e]);
+                acc += (((sgn >> e) & 1) ? -xa : xa) + (((sgn >> (8 + e)) & 1) ? -xb : xb);
+            }
+        }
+        if (!live) continue;
+        if (a.mode == 1) { a.acc[I] = acc; continue; }
+        if (a.mode == 2) { a.acc[I] += acc; continue; }
+        if (a.mode == 3) acc += a.acc[I];
+        a.sigma[I] = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                         : scalbn(__ll2double_rn(acc), u) + a.e_core * a.C[I];
+    }
+}
+
+inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+uint16_t half_bits_of_small_int(int d) {  // IEEE binary16 of an integer |d| <= 1024 (exact)
+    if (d == 0) return 0;
+    const uint16_t sign = d < 0 ? 0x8000 : 0;
+    unsigned m = (unsigned)(d < 0 ? -d : d);
+    int e = 31 - __builtin_clz(m);
+    const unsigned mant = (m << (10 - e)) & 0x3FF;
+    return (uint16_t)(sign | ((unsigned)(e + 15) << 10) | mant);
+}
+
+// Shared tables of the contraction kernel: target block offsets [n_pat_a * n_pat_b],
+// string counts [n_pat_b], one row-offset table [n_pat_b] per producer warp (int32),
+// padded to 16 bytes.
+size_t dz_table_bytes(const fci_das_layout &L, int pw) {
+    return (((size_t)L.n_pat_a * L.n_pat_b + (size_t)(1 + pw) * L.n_pat_b) * 4 + 15) & ~(size_t)15;
+}
+
+// Shared tables of the scatter kernel (256 threads: 8 row-offset tables).
+size_t dz_scatter_table_bytes(const fci_das_layout &L) { return dz_table_bytes(L, 8); }
+
+int64_t dz_nloc(const std::vector<int64_t> &nstr) {
+    int64_t t = 0;
+    for (int64_t v : nstr) t += v;
+    return t;
+}
+
+struct DzGeom {
+    int Np, KC, KCH, PW, ring, g_slice_bytes, slot_bytes, tab_off;
+    size_t smem;
+};
+
+// Shared-memory plan for a K-chunk of kch cores and pw producer warps: G slices, the
+// ring (two slots at least, up to four), the tables, the barriers.
+bool dz_geom_for(const fci_context *h, int s, int kch, int pw, DzGeom &g) {
+    const fci_das_layout &L = h->das;
+    g.Np = h->npair_pad;
+    g.KC = g.Np / 8;
+    g.g_slice_bytes = g.Np * g.KC * 16;
+    if (kch <= 0 || g.KC % kch || kch % (pw / 4)) return false;
+    const size_t tabs = dz_table_bytes(L, pw);
+    const int slot = s * DZ_TILE * kch * 16;
+    const size_t fixed = 1024 + (size_t)s * g.g_slice_bytes + tabs + sizeof(DzShared) + 64;
+    if (fixed + 2 * (size_t)slot > DZ_SMEM_MAX) return false;
+    g.KCH = kch;
+    g.PW = pw;
+    g.slot_bytes = slot;
+    g.ring = (int)std::min<size_t>(DZ_MAX_RING, (DZ_SMEM_MAX - fixed) / slot);
+    g.tab_off = s * g.g_slice_bytes + g.ring * slot;
+    g.smem = fixed + (size_t)g.ring * slot;
+    return true;
+}
+
+// Kernel configurations (K-chunk cores, producer warps) that exist.
+constexpr int DZ_CONFIGS[][2] = {{6, 12}, {6, 8}, {4, 8}, {2, 8}};
+
+// The configuration of this handle: the one the tuner chose (fci_tune_sigma), else
+// FCI_DZ_CONFIG="kch,pw" from the environment, else the first configuration in the
+// list above that fits.
+bool dz_geom(const fci_context *h, int s, DzGeom &g) {
+    const fci_das_layout &L = h->das;
+    int want_k = 0, want_p = 0;
+    if (L.dz_tuned_slices == s) {
+        want_k = L.dz_tuned_kch;
+        want_p = L.dz_tuned_pw;
+    } else if (const char *env = getenv("FCI_DZ_CONFIG")) {
+        if (sscanf(env, "%d,%d", &want_k, &want_p) != 2) want_k = want_p = 0;
+    }
+    for (const auto &c : DZ_CONFIGS)
+        if (c[0] == want_k && c[1] == want_p && dz_geom_for(h, s, want_k, want_p, g)) return true;
+    for (const auto &c : DZ_CONFIGS)
+        if (dz_geom_for(h, s, c[0], c[1], g)) return true;
+    return false;
+}
+
+}  // namespace
+
+int dz_check(fci_context *h, int s) {
+    const fci_das_layout &L = h->das;
+    if (h->dtype != FCI_R64) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real integrals");
+    if (s < 2 || s > 3)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED,
+                        "the DAS split path takes 2 or 3 slices (s level accumulators of n_pair columns in TMEM); "
+                        "use FCI_PREC_FP64 for the FP64 phase");
+    if (s * h->npair_pad > 512)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices x %d pair columns exceed the 512 TMEM columns", s,
+                        h->npair_pad);
+    if (L.n_pat_a > 256 || L.n_pat_b > 256) return fci_fail(h, FCI_ERR_UNSUPPORTED, "more than 256 patterns per spin");
+    if (L.n_cat_int > 32767) return fci_fail(h, FCI_ERR_UNSUPPORTED, "more than 32767 categories");
+    if (L.n_det_int >= ((int64_t)1 << 30))
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "the split path takes < 2^30 intermediate determinants");
+    for (int64_t v : L.pat_nstr_a)
+        if (v > DZ_LOC_MASK) return fci_fail(h, FCI_ERR_UNSUPPORTED, "a pattern has more than 2^22 strings");
+    for (int64_t v : L.pat_nstr_b)
+        if (v > DZ_LOC_MASK) return fci_fail(h, FCI_ERR_UNSUPPORTED, "a pattern has more than 2^22 strings");
+    DzGeom g;
+    if (!dz_geom(h, s, g)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit in shared memory", s);
+    return FCI_OK;
+}
+
+namespace {
+
+// G digit slices (B operand: N = pair rows pq, K = pair columns rs, canonical K-major
+// core matrices), the packed replacement tables and the block-offset table.
+int dz_prepare(fci_context *h, int s, cudaStream_t st) {
+    fci_das_layout &L = h->das;
+    int rc = dz_check(h, s);
+    if (rc) return rc;
+    if (!L.d_dz_rep_a) {
+        const int Np = h->npair_pad;
+        const int64_t nla = dz_nloc(L.pat_nstr_a), nlb = dz_nloc(L.pat_nstr_b);
+        rc = fci_dev_alloc(h, (void **)&L.d_dz_rep_a, (size_t)Np * nla * 4);
+        if (!rc) rc = fci_dev_alloc(h, (void **)&L.d_dz_rep_b, (size_t)Np * nlb * 4);
+        if (!rc) rc = fci_dev_alloc(h, (void **)&L.d_dz_base, (size_t)(2 * L.n_pat_a * L.n_pat_b + L.n_pat_b) * 4);
+        if (rc) return rc;
+        k_dz_rep<<<152 * 8, 256, 0, st>>>(h->d_pair_a, h->nsa, Np, L.d_str_of_loc_a, nla, L.d_pat_of_a, L.d_loc_a,
+                                          L.d_dz_rep_a);
+        k_dz_rep<<<152 * 8, 256, 0, st>>>(h->d_pair_b, h->nsb, Np, L.d_str_of_loc_b, nlb, L.d_pat_of_b, L.d_loc_b,
+                                          L.d_dz_rep_b);
+        FCI_CUDA(h, cudaGetLastError());
+        // [target block offsets | intermediate block offsets | string counts], int32
+        const size_t npab = (size_t)L.n_pat_a * L.n_pat_b;
+        std::vector<int32_t> tb(2 * npab + L.n_pat_b, -1);
+        for (int c = 0; c < L.n_cat_int; ++c) {
+            const size_t k = (size_t)L.cat_pa[c] * L.n_pat_b + L.cat_pb[c];
+            if (c < L.n_cat) tb[k] = (int32_t)L.cat_off[c];
+            tb[npab + k] = (int32_t)L.cat_off[c];
+        }
+        for (int b = 0; b < L.n_pat_b; ++b) tb[2 * npab + b] = (int32_t)L.pat_nstr_b[b];
+        FCI_CUDA(h, cudaMemcpy(L.d_dz_base, tb.data(), tb.size() * 4, cudaMemcpyHostToDevice));
+    }
+    if (L.dz_slices != s || !L.d_dz_G) {
+        const int np = h->npair, Np = h->npair_pad, KC = Np / 8;
+        std::vector<double> G((size_t)np * np);
+        if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fci_cuda_check(h, cudaGetLastError(), "G download");
+        double gmax = 0.0;
+        for (double v : G) gmax = std::max(gmax, fabs(v));
+        int eG = 0;
+        if (gmax > 0) frexp(gmax, &eG);  // gmax < 2^eG
+        const int shG = 8 * s - 2 - eG;
+        const uint64_t bias = 0x8080808080808080ull >> (8 * (8 - s));
+        const size_t slice = (size_t)Np * KC * 16;
+        std::vector<uint16_t> img(slice / 2 * s, 0);
+        for (int pq = 0; pq < Np; ++pq)
+            for (int rs = 0; rs < Np; ++rs) {
+                int64_t gi = 0;
+                if (pq < np && rs < np) gi = llrint(ldexp(G[(size_t)pq * np + rs], shG));
+                const uint64_t y = (uint64_t)gi + bias;
+                const size_t off = ((size_t)(pq >> 3) * KC + (rs >> 3)) * 128 + (pq & 7) * 16 + (rs & 7) * 2;
+                for (int j = 0; j < s; ++j) img[(j * slice + off) / 2] = half_bits_of_small_int((int)((y >> (8 * j)) & 0xFF) - 128);
+            }
+        fci_dev_free(L.d_dz_G);
+        L.d_dz_G = nullptr;
+        L.dz_slices = 0;
+        rc = fci_dev_alloc(h, &L.d_dz_G, img.size() * 2);
+        if (rc) return rc;
+        FCI_CUDA(h, cudaMemcpy(L.d_dz_G, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
+        L.dz_slices = s;
+        L.dz_shG = shG;
+    }
+    return FCI_OK;
+}
+
+// Intermediate-space chunk: whole categories whose E fits the cap (a single category
+// larger than the cap is a chunk of its own).  FCI_DAS_CHUNK_DETS overrides the cap
+// (in determinants) so tests can force several chunks on small problems.
+int64_t dz_chunk_cap(const fci_context *h) {
+    const char *env = getenv("FCI_DAS_CHUNK_DETS");
+    if (env && atoll(env) > 0) return atoll(env);
+    const int64_t cap_bytes = (int64_t)96 << 30;
+    return cap_bytes / (4 * (int64_t)h->npair);
+}
+
+void dz_chunks(const fci_context *h, std::vector<std::pair<int, int>> &out, int64_t &max_len) {
+    const fci_das_layout &L = h->das;
+    const int64_t cap = dz_chunk_cap(h);
+    out.clear();
+    max_len = 0;
+    int c0 = 0;
+    while (c0 < L.n_cat_int) {
+        int c1 = c0 + 1;
+        while (c1 < L.n_cat_int && L.cat_off[c1 + 1] - L.cat_off[c0] <= cap) ++c1;
+        out.push_back({c0, c1});
+        max_len = std::max(max_len, L.cat_off[c1] - L.cat_off[c0]);
+        c0 = c1;
+    }
+}
+
+struct DzJob {
+    fci_context *h;
+    const double *C;
+    double *sigma;
+    int32_t *Cint;
+    float *E;
+    int64_t *acc;
+    int *shC, *status;
+    std::vector<std::pair<int, int>> chunks;
+};
+
+int dz_prepare_job(fci_context *h, const double *C, double *sigma, int s, void *ws, cudaStream_t st, DzJob &j) {
+    int rc = dz_prepare(h, s, st);
+    if (rc) return rc;
+    const fci_das_layout &L = h->das;
+    int64_t max_len = 0;
+    dz_chunks(h, j.chunks, max_len);
+    char *p = (char *)ws;
+    j.h = h;
+    j.C = C;
+    j.sigma = sigma;
+    j.Cint = (int32_t *)p;
+    p += al256((size_t)L.n_det * 4);
+    j.E = (float *)p;
+    p += al256((size_t)ceil_div(max_len, DZ_TILE) * h->npair * DZ_TILE * 4);
+    j.acc = nullptr;
+    if (j.chunks.size() > 1) {
+        j.acc = (int64_t *)p;
+        p += al256((size_t)L.n_det * 8);
+    }
+    unsigned long long *maxbits = (unsigned long long *)p;
+    j.shC = (int *)(p + 8);
+    j.status = (int *)(p + 16);
+    h->last_status = j.status;
+    phase_scope ps(h, st, FCI_PHASE_OTHER, 2);
+    FCI_CUDA(h, cudaMemsetAsync(p, 0, 256, st));
+    const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(L.n_det, 256), 152 * 8);
+    k_dz_absmax<<<nb, 256, 0, st>>>(C, L.n_det, maxbits);
+    k_dz_to_fixed<<<nb, 256, 0, st>>>(C, L.n_det, s, maxbits, j.Cint, j.shC);
+    FCI_CUDA(h, cudaGetLastError());
+    return FCI_OK;
+}
+
+void dz_params(const DzJob &j, int s, const DzGeom &g, int chunk, DzParams &prm) {
+    const fci_context *h = j.h;
+    const fci_das_layout &L = h->das;
+    const int c0 = j.chunks[chunk].first, c1 = j.chunks[chunk].second;
+    prm.a0 = L.cat_off[c0];
+    prm.len = L.cat_off[c1] - L.cat_off[c0];
+    prm.n_det = L.n_det;
+    prm.nla = dz_nloc(L.pat_nstr_a);
+    prm.nlb = dz_nloc(L.pat_nstr_b);
+    prm.n_cat_int = L.n_cat_int;
+    prm.n_pat_a = L.n_pat_a;
+    prm.n_pat_b = L.n_pat_b;
+    prm.npair = h->npair;
+    prm.Np = g.Np;
+    prm.KC = g.KC;
+    prm.ring = g.ring;
+    prm.g_slice_bytes = g.g_slice_bytes;
+    prm.slot_bytes = g.slot_bytes;
+    prm.tab_off = g.tab_off;
+    prm.repA = L.d_dz_rep_a;
+    prm.repB = L.d_dz_rep_b;
+    prm.base_tgt = L.d_dz_base;
+    prm.nstr_b32 = L.d_dz_base + 2 * (size_t)L.n_pat_a * L.n_pat_b;
+    prm.cat_off = L.d_cat_off;
+    prm.cat_pa = L.d_cat_pa;
+    prm.cat_pb = L.d_cat_pb;
+    prm.locbase_a = L.d_pat_locbase_a;
+    prm.locbase_b = L.d_pat_locbase_b;
+    prm.Cint = j.Cint;
+    prm.Gimg = (const uint4 *)L.d_dz_G;
+    prm.E = j.E;
+    prm.status = j.status;
+    const char *to = getenv("FCI_WAIT_TIMEOUT_MS");
+    const double ms = to ? atof(to) : 2000.0;
+    prm.timeout_cycles = (long long)(ms * 2.1e6);
+    (void)s;
+}
+
+template <int S>
+void (*dz_kernel(int kch, int pw))(const DzGroup) {
+    if (kch == 6 && pw == 12) return k_oz_das<S, 6, 12>;
+    if (kch == 6 && pw == 8) return k_oz_das<S, 6, 8>;
+    if (kch == 4 && pw == 8) return k_oz_das<S, 4, 8>;
+    if (kch == 2 && pw == 8) return k_oz_das<S, 2, 8>;
+    return nullptr;
+}
+
+int dz_launch(fci_context *h, const DzGroup &grp, int s, const DzGeom &g, size_t smem, cudaStream_t st) {
+    void (*kern)(const DzGroup) = s == 2 ? dz_kernel<2>(g.KCH, g.PW) : s == 3 ? dz_kernel<3>(g.KCH, g.PW) : nullptr;
+    if (!kern) return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d, K-chunk %d, %d producer warps", s, g.KCH, g.PW);
+    FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
+    kern<<<grp.cta_start[grp.n_jobs], dz_threads(g.PW), smem, st>>>(grp);
+    FCI_CUDA(h, cudaGetLastError());
+    return FCI_OK;
+}
+
+int dz_scatter(const DzJob &j, int s, int chunk, cudaStream_t st) {
+    fci_context *h = j.h;
+    const fci_das_layout &L = h->das;
+    DzScatter a;
+    const int c0 = j.chunks[chunk].first, c1 = j.chunks[chunk].second;
+    const int nchunks = (int)j.chunks.size();
+    a.n_det = L.n_det;
+    a.nla = (int)dz_nloc(L.pat_nstr_a);
+    a.nlb = (int)dz_nloc(L.pat_nstr_b);
+    a.a0 = L.cat_off[c0];
+    a.len = L.cat_off[c1] - L.cat_off[c0];
+    a.n_cat = L.n_cat;
+    a.n_pat_a = L.n_pat_a;
+    a.n_pat_b = L.n_pat_b;
+    a.npair = h->npair;
+    a.repA = L.d_dz_rep_a;
+    a.repB = L.d_dz_rep_b;
+    a.base_int = L.d_dz_base + (size_t)L.n_pat_a * L.n_pat_b;
+    a.nstr_b32 = L.d_dz_base + 2 * (size_t)L.n_pat_a * L.n_pat_b;
+    a.cat_off = L.d_cat_off;
+    a.locbase_a = L.d_pat_locbase_a;
+    a.locbase_b = L.d_pat_locbase_b;
+    a.cat_pa = L.d_cat_pa;
+    a.cat_pb = L.d_cat_pb;
+    a.E = j.E;
+    a.C = j.C;
+    a.e_core = h->e_core;
+    a.ushift = 8 * (s - 1) - L.dz_shG;
+    a.shC = j.shC;
+    a.status = j.status;
+    a.mode = nchunks == 1 ? 0 : chunk == 0 ? 1 : chunk == nchunks - 1 ? 3 : 2;
+    a.acc = j.acc;
+    a.sigma = j.sigma;
+    const size_t smem = dz_scatter_table_bytes(L);
+    if (smem > 48 * 1024) FCI_CUDA(h, cudaFuncSetAttribute(k_dz_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.n_det, 256), 152 * 8));
+    k_dz_scatter<<<nb, 256, smem, st>>>(a);
+    FCI_CUDA(h, cudaGetLastError());
+    return FCI_OK;
+}
+
+int dz_num_sms(fci_context *h, int *nsm) {
+    FCI_CUDA(h, cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, h->device));
+    return FCI_OK;
+}
+
+}  // namespace
+
+void dz_free(fci_das_layout &L) {
+    fci_dev_free(L.d_dz_rep_a);
+    fci_dev_free(L.d_dz_rep_b);
+    fci_dev_free(L.d_dz_base);
+    fci_dev_free(L.d_dz_G);
+    L.d_dz_rep_a = L.d_dz_rep_b = nullptr;
+    L.d_dz_base = nullptr;
+    L.d_dz_G = nullptr;
+    L.dz_slices = 0;
+}
+
+size_t dz_workspace_bytes(const fci_context *h, int s) {
+    (void)s;
+    std::vector<std::pair<int, int>> ch;
+    int64_t max_len = 0;
+    dz_chunks(h, ch, max_len);
+    size_t b = al256((size_t)h->das.n_det * 4) + al256((size_t)ceil_div(max_len, DZ_TILE) * h->npair * DZ_TILE * 4);
+    if (ch.size() > 1) b += al256((size_t)h->das.n_det * 8);
+    return b + 256;
+}
+
+int dz_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, size_t ws_bytes, cudaStream_t st) {
+    (void)ws_bytes;
+    DzJob j;
+    int rc = dz_prepare_job(h, C, sigma, s, ws, st, j);
+    if (rc) return rc;
+    DzGeom g;
+    dz_geom(h, s, g);
+    int nsm = 0;
+    if ((rc = dz_num_sms(h, &nsm))) return rc;
+    for (int c = 0; c < (int)j.chunks.size(); ++c) {
+        DzGroup grp;
+        dz_params(j, s, g, c, grp.job[0]);
+        grp.n_jobs = 1;
+        grp.cta_start[0] = 0;
+        grp.cta_start[1] = (int)std::max<int64_t>(1, std::min<int64_t>(nsm, ceil_div(grp.job[0].len, DZ_TILE)));
+        if ((rc = dz_launch(h, grp, s, g, g.smem, st))) return rc;
+        if ((rc = dz_scatter(j, s, c, st))) return rc;
+    }
+    return FCI_OK;
+}
+
+// Several DAS problems with the same slice count and shared-memory plan in one
+// persistent contraction launch (CTAs in proportion to tiles, at least one per job);
+// problems whose intermediate space takes several chunks run on their own.
+int dz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
+                   int s, cudaStream_t st) {
+    std::vector<int> single;
+    for (int i = 0; i < n; ++i) {
+        std::vector<std::pair<int, int>> ch;
+        int64_t ml = 0;
+        int rc = dz_check(hs[i], s);
+        if (rc) return rc;
+        dz_chunks(hs[i], ch, ml);
+        if (ch.size() > 1) {
+            if ((rc = dz_sigma(hs[i], Cs[i], sigmas[i], s, wss[i], 0, st))) return rc;
+        } else {
+            single.push_back(i);
+        }
+    }
+    int nsm = 0;
+    if (single.empty()) return FCI_OK;
+    int rc = dz_num_sms(hs[single[0]], &nsm);
+    if (rc) return rc;
+    std::vector<char> done(single.size(), 0);
+    for (size_t a = 0; a < single.size(); ++a) {
+        if (done[a]) continue;
+        DzGeom ga;
+        dz_geom(hs[single[a]], s, ga);
+        // jobs sharing the K-chunk width (the kernel's template argument)
+        std::vector<int> grp_idx;
+        for (size_t b = a; b < single.size() && (int)grp_idx.size() < std::min(DZ_MAX_JOBS, nsm); ++b) {
+            if (done[b]) continue;
+            DzGeom gb;
+            dz_geom(hs[single[b]], s, gb);
+            if (gb.KCH != ga.KCH || gb.PW != ga.PW) continue;
+            grp_idx.push_back((int)b);
+            done[b] = 1;
+        }
+        const int m = (int)grp_idx.size();
+        std::vector<DzJob> jobs(m);
+        DzGroup grp;
+        size_t smem = 0;
+        int64_t tiles[DZ_MAX_JOBS], total = 0;
+        for (int k = 0; k < m; ++k) {
+            const int i = single[grp_idx[k]];
+            if ((rc = dz_prepare_job(hs[i], Cs[i], sigmas[i], s, wss[i], st, jobs[k]))) return rc;
+            DzGeom g;
+            dz_geom(hs[i], s, g);
+            dz_params(jobs[k], s, g, 0, grp.job[k]);
+            smem = std::max(smem, g.smem);
+            tiles[k] = std::max<int64_t>(1, ceil_div(grp.job[k].len, DZ_TILE));
+            total += tiles[k];
+        }
+        int ctas[DZ_MAX_JOBS], used = 0;
+        for (int k = 0; k < m; ++k) {
+            ctas[k] = (int)std::max<int64_t>(1, std::min<int64_t>(tiles[k], (int64_t)(nsm - m) * tiles[k] / total + 1));
+            used += ctas[k];
+        }
+        while (used > nsm) {
+            int kmax = 0;
+            for (int k = 1; k < m; ++k) if (ctas[k] > ctas[kmax]) kmax = k;
+            if (ctas[kmax] <= 1) break;
+            --ctas[kmax];
+            --used;
+        }
+        grp.n_jobs = m;
+        grp.cta_start[0] = 0;
+        for (int k = 0; k < m; ++k) grp.cta_start[k + 1] = grp.cta_start[k] + ctas[k];
+        if ((rc = dz_launch(hs[single[grp_idx[0]]], grp, s, ga, smem, st))) return rc;
+        for (int k = 0; k < m; ++k)
+            if ((rc = dz_scatter(jobs[k], s, 0, st))) return rc;
+    }
+    return FCI_OK;
+}

@@ -99,17 +99,21 @@ class Server:
     tol_residual: float = 1e-5
     tol_energy: float = 1e-9
     split_slices: int = 3             # first phase of mixed requests
-    final_slices: int = 6             # FP64-class correction phase (error < 1e-11 of ||sigma||)
+    final_slices: int = 6             # FP64-class correction phase of FCI requests (error < 1e-11
+                                      # of ||sigma||); DAS requests correct in FP64
     max_iter: int = 300
     log: list = field(default_factory=list)
 
     def _opts(self, f: fci.FCI, req: Request):
-        split_ok = req.kind == "fci" and req.n <= 15
-        if req.mixed and split_ok:
-            return f.davidson_opts(max_iter=self.max_iter, tol_residual=self.tol_residual, tol_energy=self.tol_energy,
-                                   precision="oz_bf16", n_slices=self.split_slices, switch_residual=1e-4,
+        kw = dict(max_iter=self.max_iter, tol_residual=self.tol_residual, tol_energy=self.tol_energy)
+        if req.mixed and req.kind == "fci" and req.n <= 15:
+            return f.davidson_opts(**kw, precision="oz_bf16", n_slices=self.split_slices, switch_residual=1e-4,
                                    final_precision="oz_bf16", final_slices=self.final_slices)
-        return f.davidson_opts(max_iter=self.max_iter, tol_residual=self.tol_residual, tol_energy=self.tol_energy)
+        if req.mixed and req.kind == "das" and req.n <= 17:
+            # the DAS split path takes at most 3 slices; the correction phase is FP64
+            return f.davidson_opts(**kw, precision="oz_bf16", n_slices=min(self.split_slices, 3),
+                                   switch_residual=1e-4, final_precision="fp64")
+        return f.davidson_opts(**kw)
 
     def _build(self, req: Request):
         h, g = synth.real_integrals(req.n, 2 * req.n, req.seed)

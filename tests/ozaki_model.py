@@ -43,7 +43,9 @@ def balanced_digits(X: np.ndarray, s: int):
     return [((Y >> np.uint64(8 * j)) & np.uint64(0xFF)).astype(np.int64) - 128 for j in range(s)]
 
 
-def sigma_model(h, g, n, na, nb, C, s, e_core=0.0):
+def sigma_model(h, g, n, na, nb, C, s, e_core=0.0, e_fp32=False):
+    """Split sigma of the FCI vector C.  e_fp32: store every E_int rounded to FP32 (round
+    to nearest even, as the DAS kernel does) and sum the stored integers."""
     G, idx = packed_contraction_matrix(h, g, na + nb)
     np_ = G.shape[0]
     gmax = np.max(np.abs(G))
@@ -91,6 +93,9 @@ def sigma_model(h, g, n, na, nb, C, s, e_core=0.0):
             hi += SL << (8 * (L - L0))
     k = 8 * (L0 - (s - 1))
     E = hi + (((lo + (1 << (k - 1))) >> k) if k > 0 else 0)
+    if e_fp32:
+        assert np.max(np.abs(E)) < 2 ** 53
+        E = E.astype(np.float32).astype(np.int64)
     # scatter: sigma_I = sum <I|E_pq|K> E[pq, K] (exact integers), then one conversion
     Em = E.reshape(np_, nsa, nsb)
     acc = np.zeros((nsa, nsb), np.int64)
@@ -107,3 +112,21 @@ def sigma_model(h, g, n, na, nb, C, s, e_core=0.0):
                     acc[:, S] += sg * Em[pp, :, T]
     u = 8 * L0 - shG - shC
     return np.ldexp(acc.reshape(-1).astype(np.float64), u) + e_core * C
+
+
+def das_sigma_model(h, g, spaces, ref, nel, max_transfer, C, s, e_core=0.0):
+    """Split sigma on the DAS layout (s <= 3, E stored in FP32).  The DAS sigma is the
+    FCI sigma of the zero-padded vector restricted to the DAS determinants (every
+    determinant one replacement away from a target one lies in the intermediate space),
+    so the model embeds C, applies sigma_model and restricts."""
+    from oracle import das as odas
+
+    n = sum(spaces)
+    dets, _ = odas.das_dets(spaces, ref, ref, nel, nel, max_transfer)
+    sa = oracle.enumerate_strings(n, nel)
+    pos = {int(x): i for i, x in enumerate(sa)}
+    mask = (1 << n) - 1
+    addr = np.array([pos[int(d) & mask] * len(sa) + pos[int(d) >> n] for d in dets], dtype=np.int64)
+    Cf = np.zeros(len(sa) ** 2)
+    Cf[addr] = C
+    return sigma_model(h, g, n, nel, nel, Cf, s, e_core=0.0, e_fp32=True)[addr] + e_core * C
