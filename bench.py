@@ -210,6 +210,13 @@ def run_ours(a, rank, world, local_rank):
         if passing:
             slices = min(passing)[1]
     n_sl = slices if prec == "oz_bf16" else 0
+    # tile shape of the split contraction for this problem, chosen by the tuner (untimed setup)
+    tuned = None
+    if prec == "oz_bf16":
+        try:
+            tuned = f.tune(C, n_sl, reps=3)
+        except fci.FCIError as e:
+            tuned = {"unavailable": str(e)[:200]}
 
     # FP64 peak of this GPU, measured in this run (cuBLAS DGEMM through torch)
     fp64_peak = None
@@ -309,30 +316,33 @@ def run_ours(a, rank, world, local_rank):
                  ("fp64", ("oz_bf16", 3))),
                 ("spinor_24s12e", lambda: _build_spinor(fci, synth), ("fp64",))):
             try:
-                g = build()
-                Nn = g.n_det
-                cx = torch.from_numpy(synth.random_vector(Nn, seed=7, complex_=g.is_complex)).to(dev)
-                row = {"n_det": Nn, "n_det_intermediate": g.info["n_det_intermediate"], "n_pair": g.info["n_pair"]}
+                fh = build()
+                Nn = fh.n_det
+                cx = torch.from_numpy(synth.random_vector(Nn, seed=7, complex_=fh.is_complex)).to(dev)
+                row = {"n_det": Nn, "n_det_intermediate": fh.info["n_det_intermediate"], "n_pair": fh.info["n_pair"]}
                 for pr in precs:
                     pname, sl = (pr, 0) if isinstance(pr, str) else pr
-                    o = g.sigma(cx, precision=pname, n_slices=sl)  # warm-up, workspace
+                    tuned_cfg = fh.tune(cx, sl, reps=2)["chosen"] if pname != "fp64" else None
+                    o = fh.sigma(cx, precision=pname, n_slices=sl)  # warm-up, workspace
                     torch.cuda.synchronize()
-                    g.set_phase_timing(True)
-                    g.phase_times(reset=True)
+                    fh.set_phase_timing(True)
+                    fh.phase_times(reset=True)
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    g.sigma(cx, precision=pname, n_slices=sl, out=o)
+                    fh.sigma(cx, precision=pname, n_slices=sl, out=o)
                     e1.record(stream)
                     e1.synchronize()
-                    ph = g.phase_times(reset=True)
-                    g.set_phase_timing(False)
+                    ph = fh.phase_times(reset=True)
+                    fh.set_phase_timing(False)
                     ms = e0.elapsed_time(e1)
                     key = pname if pname == "fp64" else f"{pname}_s{sl}"
                     cms = ph["contract"]["ms"]
                     m_rows = row["n_pair"]
-                    flops = (8.0 if g.is_complex else 2.0) * m_rows * m_rows * row["n_det_intermediate"]
+                    flops = (8.0 if fh.is_complex else 2.0) * m_rows * m_rows * row["n_det_intermediate"]
                     rec = {"ms": ms, "det_sigma_per_s": Nn / (ms * 1e-3),
                            "phases_ms": {k: v["ms"] for k, v in ph.items()}}
+                    if tuned_cfg:
+                        rec["tuned"] = tuned_cfg
                     if pname == "fp64":
                         rec["contract_tflops"] = flops / (cms * 1e-3) / 1e12 if cms > 0 else None
                         rec["contract_frac_of_fp64_peak"] = (rec["contract_tflops"] / fp64_peak
@@ -340,7 +350,7 @@ def run_ours(a, rank, world, local_rank):
                     else:
                         # executed MMA work of the split kernels (padded shapes, s(s+1)/2 products)
                         kp = -(-m_rows // 16) * 16
-                        if g.info["n_categories"] > 0:  # DAS: 128-determinant tiles x N = K = padded pairs
+                        if fh.info["n_categories"] > 0:  # DAS: 128-determinant tiles x N = K = padded pairs
                             ex = 2.0 * (-(-row["n_det_intermediate"] // 128) * 128) * kp * kp
                         else:  # alpha/beta: M = 128 pair rows, 64-determinant tiles
                             ex = 2.0 * 128 * kp * (-(-Nn // 64) * 64)
@@ -353,7 +363,7 @@ def run_ours(a, rank, world, local_rank):
                             rec["speedup_vs_fp64"] = s64["ms"] / ms
                     row[key] = rec
                 config_runs[name] = row
-                g.close()
+                fh.close()
                 del cx, o
                 torch.cuda.empty_cache()
             except Exception as e:  # report, do not abort the benchmark
@@ -418,8 +428,10 @@ def run_ours(a, rank, world, local_rank):
         "warmup": a.warmup, "ms_per_step": 1e3 * T / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == "fp64" else f"f64 (bf16 x{n_sl} split, int64 accumulate)",
         "data": "synthetic (seeded integrals and vector)",
-        "config": {"workload": f"{a.workload}: FCI(14e,14o), N={N}, 28 Cholesky vectors, seed 2",
+        "config": {"workload": f"{a.workload}: FCI({w['na'] + w['nb']}e,{w['n']}o), N={N}, "
+                               f"{w['n_chol']} Cholesky vectors, seed {w['seed']}",
                    "precision": prec, "n_slices": n_sl, "parallelism": f"replicas x{world}",
+                   "autotune": tuned,
                    "l2": "256 MB buffer written between timed steps (untimed)",
                    "setup_s": setup_s},
         "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},

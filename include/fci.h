@@ -226,6 +226,28 @@ int fci_sigma_graph(fci_handle h, const void *C, void *sigma, int precision, int
 /* Drop the handle's cached sigma graphs (e.g. before freeing the buffers they name). */
 int fci_clear_graphs(fci_handle h);
 
+/* Autotuning of the split-precision contraction's tile shape for this problem.
+ * Candidates: alpha/beta strings, the determinants per tile of the MMA (64 or 32);
+ * DAS layout, the K-chunk width of the operand ring (6, 4 or 2 cores of 8 pairs) and
+ * the number of producer warps (12 or 8), where shared memory allows.  Every candidate
+ * runs one untimed and `reps` timed FCI_PREC_OZ_BF16 sigma builds of C (DEVICE, n_det
+ * values; sigma is overwritten) with n_slices slices, timed by CUDA events on `stream`;
+ * the fastest is kept in the handle and used by every later split sigma with n_slices
+ * slices (the results do not depend on it: the arithmetic is exact integer).  Cached
+ * sigma graphs are dropped.  Host-synchronous.  `report` (may be NULL) receives the
+ * candidates, their mean times and the choice.  FCI_ERR_UNSUPPORTED for spinor strings
+ * or slice counts the split path does not take. */
+typedef struct {
+    int n_candidates;
+    int chosen;          /* index of the kept candidate */
+    int param_a[8];      /* alpha/beta: determinants per tile; DAS: K-chunk cores */
+    int param_b[8];      /* alpha/beta: 0; DAS: producer warps */
+    double ms[8];        /* mean time of one sigma build */
+} fci_tune_report;
+
+int fci_tune_sigma(fci_handle h, int n_slices, const void *C, void *sigma, void *workspace,
+                   size_t workspace_bytes, int reps, fci_stream stream, fci_tune_report *report);
+
 /* ------------------------------------------------- grouped sigma, step-wise Davidson */
 
 /* One sigma build of a batch: sigma = H C for one vector of the problem held by handle. */

@@ -597,6 +597,74 @@ int fci_sigma_graph(fci_handle h, const void *C, void *sigma, int precision, int
     return FCI_OK;
 }
 
+int fci_tune_sigma(fci_handle h, int n_slices, const void *C, void *sigma, void *ws, size_t ws_bytes, int reps,
+                   fci_stream stream, fci_tune_report *report) {
+    if (!h) return fci_fail(nullptr, FCI_ERR_ARG, "NULL handle");
+    if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "no strings built");
+    if (h->mode == FCI_MODE_SPINOR || h->dtype != FCI_R64)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real alpha/beta or DAS problems");
+    if (!C || !sigma || reps < 1) return fci_fail(h, FCI_ERR_ARG, "bad C/sigma/reps");
+    const size_t need = sigma_ws_bytes(h, FCI_PREC_OZ_BF16, n_slices);
+    if (ws_bytes < need || !ws || ((uintptr_t)ws & 255)) return fci_fail(h, FCI_ERR_ARG, "workspace too small or misaligned");
+    int rc = set_dev(h);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int a[8] = {0}, b[8] = {0}, n = 0;
+    if (h->das_active) {
+        if ((rc = dz_check(h, n_slices))) return rc;
+        n = dz_tune_candidates(h, n_slices, a, b, 8);
+    } else {
+        if ((rc = oz_prepare_G(h, n_slices))) return rc;
+        n = oz_tune_candidates(h, n_slices, a, 8);
+    }
+    if (n == 0) return fci_fail(h, FCI_ERR_UNSUPPORTED, "no kernel configuration fits %d slices", n_slices);
+    drop_graphs(h);
+    cudaEvent_t e0, e1;
+    FCI_CUDA(h, cudaEventCreate(&e0));
+    FCI_CUDA(h, cudaEventCreate(&e1));
+    double ms[8];
+    int best = 0;
+    for (int i = 0; i < n; ++i) {
+        if (h->das_active) dz_set_config(h, n_slices, a[i], b[i]);
+        else oz_set_config(h, n_slices, a[i]);
+        rc = sigma_dispatch(h, C, sigma, FCI_PREC_OZ_BF16, n_slices, ws, ws_bytes, s);  // untimed
+        if (!rc) rc = fci_cuda_check(h, cudaEventRecord(e0, s), "event");
+        for (int r = 0; r < reps && !rc; ++r) rc = sigma_dispatch(h, C, sigma, FCI_PREC_OZ_BF16, n_slices, ws, ws_bytes, s);
+        if (!rc) rc = fci_cuda_check(h, cudaEventRecord(e1, s), "event");
+        if (!rc) rc = fci_cuda_check(h, cudaEventSynchronize(e1), "sync");
+        if (!rc && h->last_status) {
+            int st = 0;
+            rc = fci_cuda_check(h, cudaMemcpy(&st, h->last_status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+            if (!rc && st) rc = fci_fail(h, st, "split-precision kernel reported status %d while tuning", st);
+        }
+        float t = 0.f;
+        if (!rc) rc = fci_cuda_check(h, cudaEventElapsedTime(&t, e0, e1), "elapsed");
+        if (rc) break;
+        ms[i] = t / reps;
+        if (ms[i] < ms[best]) best = i;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {  // leave the default configuration
+        if (h->das_active) dz_set_config(h, n_slices, 0, 0);
+        else oz_set_config(h, n_slices, 0);
+        return rc;
+    }
+    if (h->das_active) dz_set_config(h, n_slices, a[best], b[best]);
+    else oz_set_config(h, n_slices, a[best]);
+    if (report) {
+        memset(report, 0, sizeof(*report));
+        report->n_candidates = n;
+        report->chosen = best;
+        for (int i = 0; i < n; ++i) {
+            report->param_a[i] = a[i];
+            report->param_b[i] = b[i];
+            report->ms[i] = ms[i];
+        }
+    }
+    return FCI_OK;
+}
+
 int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream) {
     if (!jobs || n_jobs < 0) return fci_fail(nullptr, FCI_ERR_ARG, "bad job list");
     if (n_jobs == 0) return FCI_OK;

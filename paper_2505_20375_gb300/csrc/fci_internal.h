@@ -102,6 +102,7 @@ struct fci_context {
     int Gs_slices = 0;
     double G_scale = 0.0;  // |G| <= 2^G_exp
     int G_exp = 0;
+    int oz_tuned_nt[9] = {0};  // determinants per tile chosen by the tuner, per slice count (0: default)
 
     fci_das_layout das;
     bool das_active = false;
@@ -202,10 +203,14 @@ int dz_sigma(fci_context *h, const double *C, double *sigma, int n_slices, void 
 int dz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
                    int s, cudaStream_t st);
 void dz_free(fci_das_layout &L);
+int dz_tune_candidates(const fci_context *h, int n_slices, int *kch, int *pw, int max);  // fitting configurations
+void dz_set_config(fci_context *h, int n_slices, int kch, int pw);                     // kch = 0: default
 int dz_check(fci_context *h, int n_slices);  // FCI_OK if the DAS split path takes this problem
 
 // ozaki.cu
 int oz_prepare_G(fci_context *h, int n_slices);
+int oz_tune_candidates(const fci_context *h, int n_slices, int *nt, int max);  // tile widths that fit
+void oz_set_config(fci_context *h, int n_slices, int nt);                     // nt = 0: default
 size_t oz_workspace_bytes(const fci_context *h, int n_slices);
 int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int n_slices, void *ws,
                  size_t ws_bytes, cudaStream_t s);

@@ -38,6 +38,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include <cuda_fp16.h>
 
@@ -53,10 +54,12 @@ constexpr int OZ_EPILOGUE_WARPS = 8;  // two per TMEM lane quadrant, 16 columns 
 constexpr int OZ_MMA_WARP = OZ_PRODUCER_WARPS + OZ_EPILOGUE_WARPS;
 constexpr int OZ_THREADS = 32 * (OZ_MMA_WARP + 1);  // 512
 constexpr int OZ_MAX_RING = 3;  // digit-plane slots (2 or 3, whatever shared memory allows)
-// Determinants per tile (the MMA's N).  A tcgen05.mma costs at least ~45 cycles to issue
-// whatever its size, so an M=128 N=32 K=16 MMA reaches only about a third of the tensor
-// rate; N=64 is the largest tile for which the s level accumulators fit in TMEM (s <= 7).
-constexpr int OZ_TILE = 64;
+// Determinants per tile (the MMA's N): 64 by default, or 32 (chosen per slice count by
+// the tuner).  A tcgen05.mma costs at least ~45 cycles to issue whatever its size, so
+// an M=128 N=32 K=16 MMA reaches only about a third of the tensor rate, but at N=32 the
+// level accumulators are double-buffered up to s = 8; N=64 is the largest tile for which
+// the s level accumulators fit in TMEM (s <= 7) and the producers' registers suffice.
+constexpr int OZ_TILE = 64;      // the largest tile (workspace sizing)
 constexpr int OZ_MAXS = 7;
 
 struct OzParams {
@@ -71,6 +74,7 @@ struct OzParams {
     long long timeout_cycles;
     int stall_test;
     int ring;  // digit-plane slots in use
+    int nt;    // determinants per tile (the kernel's NT)
 };
 
 // Several sigma builds in one launch: CTAs [cta_start[j], cta_start[j+1]) serve job j.
@@ -401,7 +405,7 @@ __global__ void k_to_fixed(const double *__restrict__ C, int64_t n, int s,
         Cint[i] = __double2ll_rn(scalbn(C[i], sh));
 }
 
-__global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, int npair,
+__global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, int npair, int log2T,
                                                      const int32_t *__restrict__ pairA,
                                                      const int32_t *__restrict__ pairB,
                                                      const int64_t *__restrict__ E, int64_t ldE,
@@ -412,8 +416,9 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
     if (ib >= nsb) return;
     const int u = ushift - *shC;
     const bool bad = *status != 0;
-    // E is tile-major: element (pq, K) at (K / T) * n_pair * T + pq * T + K % T, T = OZ_TILE
-    const int64_t tstride = (int64_t)npair * OZ_TILE;
+    // E is tile-major: element (pq, K) at (K / T) * n_pair * T + pq * T + K % T, T = 2^log2T
+    const int64_t tstride = (int64_t)npair << log2T;
+    const int64_t tmask = ((int64_t)1 << log2T) - 1;
     for (int64_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
         const int64_t det = ia * nsb + ib;
         int64_t acc = 0;
@@ -421,13 +426,13 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
             const int32_t ea = __ldg(pairA + (int64_t)pp * nsa + ia);
             if (ea >= 0) {
                 const int64_t K = (int64_t)(ea >> 1) * nsb + ib;
-                const int64_t e = __ldg(E + (K / OZ_TILE) * tstride + pp * OZ_TILE + (K % OZ_TILE));
+                const int64_t e = __ldg(E + (K >> log2T) * tstride + ((int64_t)pp << log2T) + (K & tmask));
                 acc += (ea & 1) ? -e : e;
             }
             const int32_t eb = __ldg(pairB + (int64_t)pp * nsb + ib);
             if (eb >= 0) {
                 const int64_t K = ia * nsb + (eb >> 1);
-                const int64_t e = __ldg(E + (K / OZ_TILE) * tstride + pp * OZ_TILE + (K % OZ_TILE));
+                const int64_t e = __ldg(E + (K >> log2T) * tstride + ((int64_t)pp << log2T) + (K & tmask));
                 acc += (eb & 1) ? -e : e;
             }
         }
@@ -440,13 +445,23 @@ inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 int oz_kc(const fci_context *h) { return ((h->npair + 15) / 16) * 2; }
 int oz_L0(int s) { return std::max(s - 1, 2 * s - 6); }
 constexpr size_t OZ_SMEM_MAX = 232448;
-size_t oz_smem_bytes(int s, int KC, int ring) {
-    return 1024 + (size_t)s * 128 * KC * 16 + (size_t)ring * OZ_TILE * KC * 16 + sizeof(OzShared);
+size_t oz_smem_bytes(int s, int KC, int ring, int nt) {
+    return 1024 + (size_t)s * 128 * KC * 16 + (size_t)ring * nt * KC * 16 + sizeof(OzShared);
 }
-int oz_ring(int s, int KC) {
-    if (oz_smem_bytes(s, KC, 3) <= OZ_SMEM_MAX) return 3;
-    if (oz_smem_bytes(s, KC, 2) <= OZ_SMEM_MAX) return 2;
+int oz_ring(int s, int KC, int nt) {
+    if (oz_smem_bytes(s, KC, 3, nt) <= OZ_SMEM_MAX) return 3;
+    if (oz_smem_bytes(s, KC, 2, nt) <= OZ_SMEM_MAX) return 2;
     return 0;
+}
+// Tile width of this handle for s slices: the tuner's choice, else FCI_OZ_TILE from the
+// environment (32 or 64), else 64.
+int oz_nt(const fci_context *h, int s) {
+    if (s >= 2 && s <= 8 && h->oz_tuned_nt[s]) return h->oz_tuned_nt[s];
+    if (const char *env = getenv("FCI_OZ_TILE")) {
+        const int v = atoi(env);
+        if (v == 32 || v == 64) return v;
+    }
+    return 64;
 }
 
 }  // namespace
@@ -469,7 +484,7 @@ int oz_prepare_G(fci_context *h, int s) {
     if (h->ndet >= ((int64_t)1 << 31)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision needs < 2^31 determinants");
     if (s < 2 || s > OZ_MAXS) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision supports 2..%d slices", OZ_MAXS);
     if (s * np > 1023) return fci_fail(h, FCI_ERR_UNSUPPORTED, "level sums would exceed 2^24");
-    if (!oz_ring(s, KC)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit in shared memory", s);
+    if (!oz_ring(s, KC, 64)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit in shared memory", s);
     std::vector<double> G((size_t)np * np);
     if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fci_cuda_check(h, cudaGetLastError(), "G download");
@@ -506,7 +521,7 @@ int oz_prepare_G(fci_context *h, int s) {
 
 size_t oz_workspace_bytes(const fci_context *h, int s) {
     (void)s;
-    const int64_t ntiles = (h->ndet + OZ_TILE - 1) / OZ_TILE;
+    const int64_t ntiles = (h->ndet + OZ_TILE - 1) / OZ_TILE;  // E for the widest tile covers the others
     return al256((size_t)h->ndet * 8) + al256((size_t)ntiles * h->npair * OZ_TILE * 8) + 256;
 }
 
@@ -555,24 +570,30 @@ static int oz_prepare_job(fci_context *h, const double *C, int s, void *ws, cuda
     prm.timeout_cycles = (long long)(ms * 2.1e6);  // cycles at up to 2.1 GHz
     const char *stall = getenv("FCI_TEST_STALL_PRODUCER");
     prm.stall_test = stall ? atoi(stall) : 0;
-    prm.ring = oz_ring(s, KC);
+    prm.nt = oz_nt(h, s);
+    prm.ring = oz_ring(s, KC, prm.nt);
     *E_out = E;
     *shC_out = shC;
     *status_out = status;
     return FCI_OK;
 }
 
-static int oz_launch_group(fci_context *h, const OzGroup &grp, int s, size_t smem, cudaStream_t st) {
-    void (*kern)(const OzGroup) = nullptr;
+template <int NT>
+static void (*oz_kernel(int s))(const OzGroup) {
     switch (s) {
-        case 2: kern = k_oz_contract<2, OZ_TILE>; break;
-        case 3: kern = k_oz_contract<3, OZ_TILE>; break;
-        case 4: kern = k_oz_contract<4, OZ_TILE>; break;
-        case 5: kern = k_oz_contract<5, OZ_TILE>; break;
-        case 6: kern = k_oz_contract<6, OZ_TILE>; break;
-        case 7: kern = k_oz_contract<7, OZ_TILE>; break;
-        default: return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d", s);
+        case 2: return k_oz_contract<2, NT>;
+        case 3: return k_oz_contract<3, NT>;
+        case 4: return k_oz_contract<4, NT>;
+        case 5: return k_oz_contract<5, NT>;
+        case 6: return k_oz_contract<6, NT>;
+        case 7: return k_oz_contract<7, NT>;
+        default: return nullptr;
     }
+}
+
+static int oz_launch_group(fci_context *h, const OzGroup &grp, int s, int nt, size_t smem, cudaStream_t st) {
+    void (*kern)(const OzGroup) = nt == 32 ? oz_kernel<32>(s) : nt == 64 ? oz_kernel<64>(s) : nullptr;
+    if (!kern) return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d, tile %d", s, nt);
     FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
     kern<<<grp.cta_start[grp.n_jobs], OZ_THREADS, smem, st>>>(grp);
@@ -585,7 +606,8 @@ static int oz_finish_job(fci_context *h, const double *C, double *sigma, const O
     phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
     const int threads = 128;
     dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
-    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, h->d_pair_a, h->d_pair_b, E, 0, C, h->e_core,
+    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, prm.nt == 32 ? 5 : 6, h->d_pair_a, h->d_pair_b, E, 0,
+                                       C, h->e_core,
                                        8 * prm.L0 - h->G_exp, shC, status, sigma);
     FCI_CUDA(h, cudaGetLastError());
     return FCI_OK;
@@ -605,19 +627,20 @@ int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws
     if (rc) return rc;
     int nsm = 0;
     if ((rc = oz_num_sms(h, &nsm))) return rc;
-    const int64_t ntiles = (h->ndet + OZ_TILE - 1) / OZ_TILE;
+    const int nt = grp.job[0].nt;
+    const int64_t ntiles = (h->ndet + nt - 1) / nt;
     grp.n_jobs = 1;
     grp.cta_start[0] = 0;
     grp.cta_start[1] = (int)std::min<int64_t>(nsm, ntiles);
-    if ((rc = oz_launch_group(h, grp, s, oz_smem_bytes(s, grp.job[0].KC, grp.job[0].ring), st))) return rc;
+    if ((rc = oz_launch_group(h, grp, s, nt, oz_smem_bytes(s, grp.job[0].KC, grp.job[0].ring, nt), st))) return rc;
     return oz_finish_job(h, C, sigma, grp.job[0], E, shC, status, st);
 }
 
-// Split-precision sigma of several problems sharing one slice count: one fixed-point
-// pre-pass per job, ONE persistent contraction launch for all jobs (CTAs shared in
-// proportion to tiles, at least one per job), one scatter per job.
-int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
-                   int s, cudaStream_t st) {
+// Split-precision sigma of several problems sharing one slice count and tile width: one
+// fixed-point pre-pass per job, ONE persistent contraction launch for all jobs (CTAs
+// shared in proportion to tiles, at least one per job), one scatter per job.
+static int oz_sigma_group_nt(fci_context *const *hs, const double *const *Cs, double *const *sigmas,
+                             void *const *wss, int n, int s, int nt, cudaStream_t st) {
     int nsm = 0;
     int rc = oz_num_sms(hs[0], &nsm);
     if (rc) return rc;
@@ -632,8 +655,8 @@ int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *cons
             fci_context *h = hs[base + j];
             if ((rc = oz_prepare_job(h, Cs[base + j], s, wss[base + j], st, grp.job[j], &E[j], &shC[j], &status[j])))
                 return rc;
-            smem = std::max(smem, oz_smem_bytes(s, grp.job[j].KC, grp.job[j].ring));
-            tiles[j] = (h->ndet + OZ_TILE - 1) / OZ_TILE;
+            smem = std::max(smem, oz_smem_bytes(s, grp.job[j].KC, grp.job[j].ring, nt));
+            tiles[j] = (h->ndet + nt - 1) / nt;
             total += tiles[j];
         }
         // CTAs in proportion to tiles, at least one per job, never more CTAs than tiles
@@ -652,11 +675,45 @@ int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *cons
         grp.n_jobs = m;
         grp.cta_start[0] = 0;
         for (int j = 0; j < m; ++j) grp.cta_start[j + 1] = grp.cta_start[j] + ctas[j];
-        if ((rc = oz_launch_group(hs[base], grp, s, smem, st))) return rc;
+        if ((rc = oz_launch_group(hs[base], grp, s, nt, smem, st))) return rc;
         for (int j = 0; j < m; ++j)
             if ((rc = oz_finish_job(hs[base + j], Cs[base + j], sigmas[base + j], grp.job[j], E[j], shC[j], status[j], st)))
                 return rc;
         base += m;
     }
     return FCI_OK;
+}
+
+// Jobs grouped by their tile width (the kernel's template argument), one launch per group.
+int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
+                   int s, cudaStream_t st) {
+    for (int nt : {64, 32}) {
+        std::vector<fci_context *> h2;
+        std::vector<const double *> c2;
+        std::vector<double *> s2;
+        std::vector<void *> w2;
+        for (int i = 0; i < n; ++i)
+            if (oz_nt(hs[i], s) == nt) {
+                h2.push_back(hs[i]);
+                c2.push_back(Cs[i]);
+                s2.push_back(sigmas[i]);
+                w2.push_back(wss[i]);
+            }
+        if (h2.empty()) continue;
+        const int rc = oz_sigma_group_nt(h2.data(), c2.data(), s2.data(), w2.data(), (int)h2.size(), s, nt, st);
+        if (rc) return rc;
+    }
+    return FCI_OK;
+}
+
+int oz_tune_candidates(const fci_context *h, int s, int *nt, int max) {
+    const int KC = oz_kc(h);
+    int n = 0;
+    for (int t : {64, 32})
+        if (n < max && s * t <= 512 && oz_ring(s, KC, t)) nt[n++] = t;
+    return n;
+}
+
+void oz_set_config(fci_context *h, int s, int nt) {
+    if (s >= 2 && s <= 8) h->oz_tuned_nt[s] = nt;
 }

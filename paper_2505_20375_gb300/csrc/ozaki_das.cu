@@ -1050,3 +1050,22 @@ int dz_sigma_group(fci_context *const *hs, const double *const *Cs, double *cons
     }
     return FCI_OK;
 }
+
+int dz_tune_candidates(const fci_context *h, int s, int *kch, int *pw, int max) {
+    int n = 0;
+    DzGeom g;
+    for (const auto &c : DZ_CONFIGS)
+        if (n < max && dz_geom_for(h, s, c[0], c[1], g)) {
+            kch[n] = c[0];
+            pw[n] = c[1];
+            ++n;
+        }
+    return n;
+}
+
+void dz_set_config(fci_context *h, int s, int kch, int pw) {
+    fci_das_layout &L = h->das;
+    L.dz_tuned_slices = kch ? s : 0;
+    L.dz_tuned_kch = kch;
+    L.dz_tuned_pw = pw;
+}

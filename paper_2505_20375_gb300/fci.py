@@ -90,6 +90,14 @@ _sigma_graph = _sig("fci_sigma_graph", [_vp, _vp, _vp, _i32, _i32, _vp, _sz, _vp
 _clear_graphs = _sig("fci_clear_graphs", [_vp])
 
 
+class fci_tune_report(ctypes.Structure):
+    _fields_ = [("n_candidates", _i32), ("chosen", _i32), ("param_a", _i32 * 8), ("param_b", _i32 * 8),
+                ("ms", _dbl * 8)]
+
+
+_tune = _sig("fci_tune_sigma", [_vp, _i32, _vp, _vp, _vp, _sz, _i32, _vp, ctypes.POINTER(fci_tune_report)])
+
+
 class fci_sigma_job(ctypes.Structure):
     _fields_ = [("handle", _vp), ("C", _vp), ("sigma", _vp), ("precision", _i32), ("n_slices", _i32),
                 ("workspace", _vp), ("workspace_bytes", _sz)]
@@ -264,6 +272,20 @@ class FCI:
 
     def clear_graphs(self):
         self._check(_clear_graphs(self._h))
+
+    def tune(self, C: torch.Tensor, n_slices: int, reps: int = 3, stream=None) -> dict:
+        """Time every tile shape of the split-precision contraction on this problem and keep
+        the fastest for later split sigma builds with n_slices slices (fci_tune_sigma)."""
+        Cd = C.to(self.device).contiguous()
+        out = torch.empty_like(Cd)
+        p, nb = self._workspace(self.sigma_workspace_bytes("oz_bf16", n_slices))
+        r = fci_tune_report()
+        self._check(_tune(self._h, n_slices, Cd.data_ptr(), out.data_ptr(), p, nb, reps, _stream(stream),
+                          ctypes.byref(r)))
+        das = bool(self.info["n_categories"])
+        cands = [({"k_chunk_cores": r.param_a[i], "producer_warps": r.param_b[i]} if das
+                  else {"dets_per_tile": r.param_a[i]}) | {"ms": r.ms[i]} for i in range(r.n_candidates)]
+        return {"n_slices": n_slices, "candidates": cands, "chosen": cands[r.chosen]}
 
     def davidson_opts(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                       precision="fp64", n_slices=6, switch_residual=1e-5, final_precision="fp64", final_slices=0,
