@@ -149,10 +149,12 @@ int fci_sigma_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slic
  *   C, sigma: DEVICE pointers, n_vec x info.n_det, vector-major, double (R64) or
  *             interleaved complex (C128); must not overlap;
  *   precision: FCI_PREC_FP64, or FCI_PREC_OZ_BF16 with n_slices 16-bit digit slices of
- *             each operand of the contraction (R64 only): alpha/beta strings take 2..7
+ *             each operand of the contraction: alpha/beta strings (R64) take 2..7
  *             slices (n_orb <= 15; 6 and 7 reach the FP64 tolerance); the DAS layout
  *             takes 2 or 3 slices (n_orb <= 17), with E stored in FP32, for the first
- *             phase of a mixed-precision solve; FCI_ERR_UNSUPPORTED otherwise;
+ *             phase of a mixed-precision solve; spinor strings with complex integrals
+ *             take 2..8 slices of 7 bits (8 reaches the FP64 tolerance);
+ *             FCI_ERR_UNSUPPORTED otherwise;
  *   workspace: DEVICE pointer, >= fci_sigma_workspace_bytes, 256-byte aligned.
  * Asynchronous on `stream`. */
 int fci_sigma(fci_handle h, const void *C, void *sigma, int n_vec, int precision,

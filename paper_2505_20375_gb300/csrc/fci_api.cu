@@ -464,8 +464,8 @@ int fci_sigma(fci_handle h, const void *C, void *sigma, int n_vec, int precision
         return fci_fail(h, FCI_ERR_ARG, "unknown precision %d", precision);
     if (precision == FCI_PREC_OZ_BF16 && (n_slices < 2 || n_slices > 8))
         return fci_fail(h, FCI_ERR_ARG, "n_slices %d outside [2, 8]", n_slices);
-    if (precision == FCI_PREC_OZ_BF16 && h->dtype != FCI_R64)
-        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real integrals only");
+    if (precision == FCI_PREC_OZ_BF16 && h->dtype != FCI_R64 && h->mode != FCI_MODE_SPINOR)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision with complex integrals needs spinor strings");
     const size_t need = sigma_ws_bytes(h, precision, n_slices);
     if (ws_bytes < need || (need && !ws)) return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes", ws_bytes, need);
     if (((uintptr_t)ws & 255) != 0) return fci_fail(h, FCI_ERR_ARG, "workspace not 256-byte aligned");
@@ -540,8 +540,9 @@ int davidson_solve(fci_handle h, const fci_davidson_opts *o, void *C_io, double 
     if (rc) return rc;
     if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "no strings built");
     if (!C_io || !energy) return fci_fail(h, FCI_ERR_ARG, "NULL C_io/energy");
-    if ((o->precision == FCI_PREC_OZ_BF16 || o->final_precision == FCI_PREC_OZ_BF16) && h->dtype != FCI_R64)
-        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real integrals only");
+    if ((o->precision == FCI_PREC_OZ_BF16 || o->final_precision == FCI_PREC_OZ_BF16) && h->dtype != FCI_R64 &&
+        h->mode != FCI_MODE_SPINOR)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision with complex integrals needs spinor strings");
     const size_t need = davidson_ws_bytes(h, o);
     if (ws_bytes < need || !ws) return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes", ws_bytes, need);
     if (((uintptr_t)ws & 255) != 0) return fci_fail(h, FCI_ERR_ARG, "workspace not 256-byte aligned");
@@ -681,7 +682,8 @@ int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream) 
         if (!j.C || !j.sigma) return fci_fail(h, FCI_ERR_ARG, "job %d: NULL vector", i);
         if (j.precision != FCI_PREC_FP64 && j.precision != FCI_PREC_OZ_BF16)
             return fci_fail(h, FCI_ERR_ARG, "job %d: unknown precision", i);
-        if (j.precision == FCI_PREC_OZ_BF16 && (j.n_slices < 2 || j.n_slices > 8 || h->dtype != FCI_R64))
+        if (j.precision == FCI_PREC_OZ_BF16 &&
+            (j.n_slices < 2 || j.n_slices > 8 || (h->dtype != FCI_R64 && h->mode != FCI_MODE_SPINOR)))
             return fci_fail(h, FCI_ERR_ARG, "job %d: bad split-precision request", i);
         const size_t need = sigma_ws_bytes(h, j.precision, j.n_slices);
         if (j.workspace_bytes < need || !j.workspace || ((uintptr_t)j.workspace & 255))
@@ -749,8 +751,9 @@ int davidson_begin(fci_handle h, const fci_davidson_opts *o, const void *C_guess
     int rc = check_opts(h, o);
     if (rc) return rc;
     if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "no strings built");
-    if ((o->precision == FCI_PREC_OZ_BF16 || o->final_precision == FCI_PREC_OZ_BF16) && h->dtype != FCI_R64)
-        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real integrals only");
+    if ((o->precision == FCI_PREC_OZ_BF16 || o->final_precision == FCI_PREC_OZ_BF16) && h->dtype != FCI_R64 &&
+        h->mode != FCI_MODE_SPINOR)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision with complex integrals needs spinor strings");
     const size_t need = davidson_ws_bytes(h, o);
     if (ws_bytes < need || !ws) return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes", ws_bytes, need);
     if (((uintptr_t)ws & 255) != 0) return fci_fail(h, FCI_ERR_ARG, "workspace not 256-byte aligned");
@@ -841,6 +844,7 @@ int fci_copy_table(fci_handle h, int table, void *dst, size_t bytes, fci_stream 
 size_t sigma_ws_bytes(const fci_context *h, int precision, int n_slices) {
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     if (h->das_active) return das_workspace_bytes(h, precision, n_slices);
+    if (precision == FCI_PREC_OZ_BF16 && h->mode == FCI_MODE_SPINOR) return cz_workspace_bytes(h, n_slices);
     if (precision == FCI_PREC_OZ_BF16) return oz_workspace_bytes(h, n_slices);
     const size_t esz = h->dtype == FCI_C128 ? 16 : 8;
     return 2 * al((size_t)h->npair * h->ndet * esz);
@@ -853,6 +857,8 @@ int sigma_dispatch(fci_context *h, const void *C, void *sigma, int precision, in
         return precision == FCI_PREC_FP64 ? das_sigma_fp64(h, (const double *)C, (double *)sigma, ws, ws_bytes, s)
                                           : das_sigma_oz(h, (const double *)C, (double *)sigma, n_slices, ws, ws_bytes, s);
     }
+    if (precision == FCI_PREC_OZ_BF16 && h->mode == FCI_MODE_SPINOR)
+        return cz_sigma(h, (const double *)C, (double *)sigma, n_slices, ws, ws_bytes, s);
     if (precision == FCI_PREC_OZ_BF16) return oz_sigma_fci(h, (const double *)C, (double *)sigma, n_slices, ws, ws_bytes, s);
     const size_t esz = h->dtype == FCI_C128 ? 16 : 8;
     double *D = (double *)ws;

@@ -207,6 +207,11 @@ int dz_tune_candidates(const fci_context *h, int n_slices, int *kch, int *pw, in
 void dz_set_config(fci_context *h, int n_slices, int kch, int pw);                     // kch = 0: default
 int dz_check(fci_context *h, int n_slices);  // FCI_OK if the DAS split path takes this problem
 
+// ozaki_cplx.cu (spinor strings, complex integrals)
+int cz_check(fci_context *h, int n_slices);
+size_t cz_workspace_bytes(const fci_context *h, int n_slices);
+int cz_sigma(fci_context *h, const double *C, double *sigma, int n_slices, void *ws, size_t ws_bytes, cudaStream_t s);
+
 // ozaki.cu
 int oz_prepare_G(fci_context *h, int n_slices);
 int oz_tune_candidates(const fci_context *h, int n_slices, int *nt, int max);  // tile widths that fit

@@ -130,3 +130,82 @@ def das_sigma_model(h, g, spaces, ref, nel, max_transfer, C, s, e_core=0.0):
     Cf = np.zeros(len(sa) ** 2)
     Cf[addr] = C
     return sigma_model(h, g, n, nel, nel, Cf, s, e_core=0.0, e_fp32=True)[addr] + e_core * C
+
+
+def complex_contraction_matrix(h, g, n_el):
+    """1/2 g' over ordered spinor pairs x = p n + q (complex integrals, no packing)."""
+    n = h.shape[0]
+    hp = h - 0.5 * np.einsum("prrq->pq", g)
+    G = 0.5 * g.reshape(n * n, n * n).astype(complex)
+    for p in range(n):
+        for q in range(n):
+            for r in range(n):
+                G[p * n + q, r * n + r] += 0.5 * hp[p, q] / n_el
+                G[r * n + r, p * n + q] += 0.5 * hp[p, q] / n_el
+    return G
+
+
+def balanced_digits7(X: np.ndarray, s: int):
+    bias = 0
+    for j in range(s):
+        bias |= 64 << (7 * j)
+    Y = X.astype(np.int64).astype(np.uint64) + np.uint64(bias)
+    return [((Y >> np.uint64(7 * j)) & np.uint64(0x7F)).astype(np.int64) - 64 for j in range(s)]
+
+
+def spinor_sigma_model(h, g, n, ne, C, s, e_core=0.0):
+    """Split sigma for spinor strings with complex integrals: the complex contraction as
+    one real product on the real embedding [[G_re, -G_im], [G_im, G_re]] (index 2x real,
+    2x + 1 imaginary part of pair x), balanced base-128 digits, top s levels, exact int64."""
+    G = complex_contraction_matrix(h, g, ne)
+    n2 = n * n
+    Gre = np.zeros((2 * n2, 2 * n2))
+    Gre[0::2, 0::2] = G.real
+    Gre[0::2, 1::2] = -G.imag
+    Gre[1::2, 0::2] = G.imag
+    Gre[1::2, 1::2] = G.real
+    eG = int(np.frexp(np.max(np.abs(Gre)))[1])
+    shG = 7 * s - 2 - eG
+    Gint = np.rint(np.ldexp(Gre, shG)).astype(np.int64)
+    cmax = max(np.max(np.abs(C.real)), np.max(np.abs(C.imag)))
+    eC = int(np.frexp(cmax)[1]) if cmax > 0 else 0
+    shC = 7 * s - 3 - eC
+    Cr = np.rint(np.ldexp(C.real, shC)).astype(np.int64)
+    Ci = np.rint(np.ldexp(C.imag, shC)).astype(np.int64)
+    t = oracle.replacement_table(n, ne)
+    N = len(C)
+    D = np.zeros((2 * n2, N), np.int64)
+    for S in range(t["target"].shape[0]):
+        for e in range(t["target"].shape[1]):
+            T, a, b, sg = t["target"][S, e], t["a"][S, e], t["b"][S, e], int(t["sign"][S, e])
+            x = a * n + b
+            D[2 * x, S] += sg * Cr[T]
+            D[2 * x + 1, S] += sg * Ci[T]
+    gd = balanced_digits7(Gint, s)
+    dd = balanced_digits7(D, s)
+    L0 = max(s - 1, 2 * s - 7)
+    lo = np.zeros_like(D)
+    hi = np.zeros_like(D)
+    for L in range(s - 1, 2 * s - 1):
+        SL = np.zeros_like(D)
+        for i in range(s):
+            j = L - i
+            if 0 <= j < s:
+                SL += gd[i] @ dd[j]
+        assert np.max(np.abs(SL)) < 2 ** 24
+        if L < L0:
+            lo += SL << (7 * (L - (s - 1)))
+        else:
+            hi += SL << (7 * (L - L0))
+    k = 7 * (L0 - (s - 1))
+    E = hi + (((lo + (1 << (k - 1))) >> k) if k > 0 else 0)
+    ar = np.zeros(N, np.int64)
+    ai = np.zeros(N, np.int64)
+    for S in range(t["target"].shape[0]):
+        for e in range(t["target"].shape[1]):
+            T, a, b, sg = t["target"][S, e], t["a"][S, e], t["b"][S, e], int(t["sign"][S, e])
+            x = a * n + b
+            ar[S] += sg * E[2 * x, T]
+            ai[S] += sg * E[2 * x + 1, T]
+    u = 7 * L0 - shG - shC
+    return np.ldexp(ar.astype(np.float64), u) + 1j * np.ldexp(ai.astype(np.float64), u) + e_core * C

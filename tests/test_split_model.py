@@ -9,12 +9,14 @@ from oracle import das as odas
 from paper_2505_20375_gb300 import synth
 
 from helpers import fci_problem, rel_inf
-from ozaki_model import das_sigma_model, sigma_model
+from ozaki_model import das_sigma_model, sigma_model, spinor_sigma_model
 
 # ||sigma_split - sigma_exact||_inf / ||sigma_exact||_inf per slice count (alpha/beta strings)
 OZ_TOL = {2: 2e-3, 3: 2e-5, 4: 1e-7, 5: 5e-10, 6: 1e-11, 7: 1e-11}
 # DAS layout (16 orbitals: 136 pair terms per contraction, E stored in FP32)
 DZ_TOL = {2: 5e-3, 3: 5e-5}
+# complex spinor strings (balanced base-128 digits: 7 bits per slice)
+CZ_TOL = {2: 1e-2, 3: 2e-4, 4: 2e-6, 5: 2e-8, 6: 2e-10, 7: 1e-11, 8: 1e-11}
 
 
 def test_fci_model_error_falls_with_slices():
@@ -49,3 +51,17 @@ def test_fp32_storage_of_E_is_below_the_split_error():
     a = sigma_model(p["h"], p["g"], 8, 4, 4, c, 3)
     b = sigma_model(p["h"], p["g"], 8, 4, 4, c, 3, e_fp32=True)
     assert 0 < rel_inf(b, a) < rel_inf(a, exact) / 20
+
+
+def test_spinor_model_error_falls_with_slices():
+    n, ne = 6, 3
+    h, g = synth.complex_integrals(n, n + 2, 4)
+    hso, gso = oracle.spinor_integrals(h, g)
+    dets = oracle.spinor_dets(n, ne)
+    c = synth.random_vector(len(dets), seed=7, complex_=True)
+    exact = oracle.sigma(hso, gso, dets, c, e_core=0.2)
+    errs = [rel_inf(spinor_sigma_model(h, g, n, ne, c, s, e_core=0.2), exact) for s in range(2, 9)]
+    for s, e in zip(range(2, 9), errs):
+        assert e <= CZ_TOL[s], (s, e)
+    for a, b in zip(errs[:5], errs[1:6]):
+        assert b < a / 30  # about 2^-7 per slice until FP64 rounding is reached
