@@ -314,15 +314,16 @@ def run_ours(a, rank, world, local_rank):
                  ("fp64", ("oz_bf16", 2), ("oz_bf16", 3))),
                 ("das_16o_4x4_8e_t1", lambda: _build_das(fci, synth, "das_16o_4x4_8e", 4),
                  ("fp64", ("oz_bf16", 3))),
-                ("spinor_24s12e", lambda: _build_spinor(fci, synth), ("fp64",))):
+                ("spinor_24s12e", lambda: _build_spinor(fci, synth), ("fp64", ("oz_bf16", 3), ("oz_bf16", 8)))):
             try:
                 fh = build()
                 Nn = fh.n_det
                 cx = torch.from_numpy(synth.random_vector(Nn, seed=7, complex_=fh.is_complex)).to(dev)
                 row = {"n_det": Nn, "n_det_intermediate": fh.info["n_det_intermediate"], "n_pair": fh.info["n_pair"]}
+                ref_out = None
                 for pr in precs:
                     pname, sl = (pr, 0) if isinstance(pr, str) else pr
-                    tuned_cfg = fh.tune(cx, sl, reps=2)["chosen"] if pname != "fp64" else None
+                    tuned_cfg = fh.tune(cx, sl, reps=2)["chosen"] if pname != "fp64" and not fh.is_complex else None
                     o = fh.sigma(cx, precision=pname, n_slices=sl)  # warm-up, workspace
                     torch.cuda.synchronize()
                     fh.set_phase_timing(True)
@@ -344,13 +345,20 @@ def run_ours(a, rank, world, local_rank):
                     if tuned_cfg:
                         rec["tuned"] = tuned_cfg
                     if pname == "fp64":
+                        ref_out = o.clone()
+                    elif ref_out is not None:
+                        fh.sync_status()
+                        rec["rel_err_vs_fp64"] = ((o - ref_out).abs().max() / ref_out.abs().max()).item()
+                    if pname == "fp64":
                         rec["contract_tflops"] = flops / (cms * 1e-3) / 1e12 if cms > 0 else None
                         rec["contract_frac_of_fp64_peak"] = (rec["contract_tflops"] / fp64_peak
                                                              if (cms > 0 and fp64_peak) else None)
                     else:
                         # executed MMA work of the split kernels (padded shapes, s(s+1)/2 products)
                         kp = -(-m_rows // 16) * 16
-                        if fh.info["n_categories"] > 0:  # DAS: 128-determinant tiles x N = K = padded pairs
+                        if fh.is_complex:  # real embedding: M = K = 2 n^2 (padded to 128 / 32), 64-det tiles
+                            ex = 2.0 * (-(-2 * m_rows // 128) * 128) * (-(-2 * m_rows // 32) * 32) * (-(-Nn // 64) * 64)
+                        elif fh.info["n_categories"] > 0:  # DAS: 128-determinant tiles x N = K = padded pairs
                             ex = 2.0 * (-(-row["n_det_intermediate"] // 128) * 128) * kp * kp
                         else:  # alpha/beta: M = 128 pair rows, 64-determinant tiles
                             ex = 2.0 * 128 * kp * (-(-Nn // 64) * 64)
@@ -364,7 +372,7 @@ def run_ours(a, rank, world, local_rank):
                     row[key] = rec
                 config_runs[name] = row
                 fh.close()
-                del cx, o
+                del cx, o, ref_out
                 torch.cuda.empty_cache()
             except Exception as e:  # report, do not abort the benchmark
                 config_runs[name] = {"unavailable": str(e)[:200]}
