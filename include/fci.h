@@ -229,7 +229,9 @@ int fci_sigma_graph(fci_handle h, const void *C, void *sigma, int precision, int
 int fci_clear_graphs(fci_handle h);
 
 /* Autotuning of the split-precision contraction's tile shape for this problem.
- * Candidates: alpha/beta strings, the determinants per tile of the MMA (64 or 32);
+ * Candidates: alpha/beta strings, the fused kernel with 64 or 32 determinants per tile
+ * of the MMA, or the two-pass path (a digit image of D written to the workspace, then a
+ * GEMM whose operand tiles arrive by cp.async.bulk);
  * DAS layout, the K-chunk width of the operand ring (6, 4 or 2 cores of 8 pairs) and
  * the number of producer warps (12 or 8), where shared memory allows.  Every candidate
  * runs one untimed and `reps` timed FCI_PREC_OZ_BF16 sigma builds of C (DEVICE, n_det
@@ -243,7 +245,7 @@ typedef struct {
     int n_candidates;
     int chosen;          /* index of the kept candidate */
     int param_a[8];      /* alpha/beta: determinants per tile; DAS: K-chunk cores */
-    int param_b[8];      /* alpha/beta: 0; DAS: producer warps */
+    int param_b[8];      /* alpha/beta: 0 fused, 1 two-pass; DAS: producer warps */
     double ms[8];        /* mean time of one sigma build */
 } fci_tune_report;
 

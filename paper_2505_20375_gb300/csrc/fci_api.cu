@@ -112,12 +112,15 @@ static void free_strings(fci_context *h) {
     fci_dev_free(h->d_pair_a); fci_dev_free(h->d_pair_b);
     fci_dev_free(h->d_G); fci_dev_free(h->d_hd); fci_dev_free(h->d_J); fci_dev_free(h->d_K);
     fci_dev_free(h->d_Gs);
+    fci_dev_free(h->d_Gt);
     h->d_str_a = h->d_str_b = nullptr;
     h->d_rep_a = h->d_rep_b = nullptr;
     h->d_pair_a = h->d_pair_b = nullptr;
     h->d_G = h->d_hd = h->d_J = h->d_K = nullptr;
     h->d_Gs = nullptr;
     h->Gs_slices = 0;
+    h->d_Gt = nullptr;
+    h->Gt_slices = 0;
     das_free(h);
     h->mode = FCI_MODE_NONE;
     h->nsa = h->nsb = h->ndet = 0;
@@ -616,7 +619,7 @@ int fci_tune_sigma(fci_handle h, int n_slices, const void *C, void *sigma, void 
         n = dz_tune_candidates(h, n_slices, a, b, 8);
     } else {
         if ((rc = oz_prepare_G(h, n_slices))) return rc;
-        n = oz_tune_candidates(h, n_slices, a, 8);
+        n = oz_tune_candidates(h, n_slices, a, b, 8);
     }
     if (n == 0) return fci_fail(h, FCI_ERR_UNSUPPORTED, "no kernel configuration fits %d slices", n_slices);
     drop_graphs(h);
@@ -627,7 +630,7 @@ int fci_tune_sigma(fci_handle h, int n_slices, const void *C, void *sigma, void 
     int best = 0;
     for (int i = 0; i < n; ++i) {
         if (h->das_active) dz_set_config(h, n_slices, a[i], b[i]);
-        else oz_set_config(h, n_slices, a[i]);
+        else oz_set_config(h, n_slices, a[i], b[i]);
         rc = sigma_dispatch(h, C, sigma, FCI_PREC_OZ_BF16, n_slices, ws, ws_bytes, s);  // untimed
         if (!rc) rc = fci_cuda_check(h, cudaEventRecord(e0, s), "event");
         for (int r = 0; r < reps && !rc; ++r) rc = sigma_dispatch(h, C, sigma, FCI_PREC_OZ_BF16, n_slices, ws, ws_bytes, s);
@@ -648,11 +651,11 @@ int fci_tune_sigma(fci_handle h, int n_slices, const void *C, void *sigma, void 
     cudaEventDestroy(e1);
     if (rc) {  // leave the default configuration
         if (h->das_active) dz_set_config(h, n_slices, 0, 0);
-        else oz_set_config(h, n_slices, 0);
+        else oz_set_config(h, n_slices, 0, 0);
         return rc;
     }
     if (h->das_active) dz_set_config(h, n_slices, a[best], b[best]);
-    else oz_set_config(h, n_slices, a[best]);
+    else oz_set_config(h, n_slices, a[best], b[best]);
     if (report) {
         memset(report, 0, sizeof(*report));
         report->n_candidates = n;

@@ -102,7 +102,10 @@ struct fci_context {
     int Gs_slices = 0;
     double G_scale = 0.0;  // |G| <= 2^G_exp
     int G_exp = 0;
-    int oz_tuned_nt[9] = {0};  // determinants per tile chosen by the tuner, per slice count (0: default)
+    int oz_tuned_nt[9] = {0};    // determinants per tile chosen by the tuner, per slice count (0: default)
+    int oz_tuned_path[9] = {0};  // 1: two-pass path (D digit image + bulk-copy GEMM) chosen by the tuner
+    void *d_Gt = nullptr;        // G digit image in the GEMM's A-tile layout (two-pass path)
+    int Gt_slices = 0;
 
     fci_das_layout das;
     bool das_active = false;
@@ -214,8 +217,8 @@ int cz_sigma(fci_context *h, const double *C, double *sigma, int n_slices, void 
 
 // ozaki.cu
 int oz_prepare_G(fci_context *h, int n_slices);
-int oz_tune_candidates(const fci_context *h, int n_slices, int *nt, int max);  // tile widths that fit
-void oz_set_config(fci_context *h, int n_slices, int nt);                     // nt = 0: default
+int oz_tune_candidates(const fci_context *h, int n_slices, int *nt, int *path, int max);  // configurations that fit
+void oz_set_config(fci_context *h, int n_slices, int nt, int path);                     // nt = 0: default
 size_t oz_workspace_bytes(const fci_context *h, int n_slices);
 int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int n_slices, void *ws,
                  size_t ws_bytes, cudaStream_t s);

@@ -43,6 +43,7 @@
 #include <cuda_fp16.h>
 
 #include "fci_internal.h"
+#include "oz_gemm.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
@@ -416,8 +417,9 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
     if (ib >= nsb) return;
     const int u = ushift - *shC;
     const bool bad = *status != 0;
-    // E is tile-major: element (pq, K) at (K / T) * n_pair * T + pq * T + K % T, T = 2^log2T
-    const int64_t tstride = (int64_t)npair << log2T;
+    // E is tile-major: element (pq, K) at (K / T) * R * T + pq * T + K % T, T = 2^log2T,
+    // R = ldE rows per tile (n_pair for the fused kernel, 128 for the two-pass GEMM)
+    const int64_t tstride = ldE << log2T;
     const int64_t tmask = ((int64_t)1 << log2T) - 1;
     for (int64_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
         const int64_t det = ia * nsb + ib;
@@ -440,6 +442,58 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
     }
 }
 
+// Two-pass path, first pass: the digit image of D for the bulk-copy GEMM.  Block (N-tile
+// nt, K-chunk kc) holds S planes of 64 determinants x 32 pairs in canonical K-major core
+// matrices; one CTA of 256 threads fills one block, thread t covering determinant t % 64
+// and pairs 8 (t / 64) .. 8 (t / 64) + 7 of the chunk (pair-table rows past n_pair_pad
+// and determinants past the end give zero digits).
+template <int S>
+__global__ void __launch_bounds__(256) k_fci_split(int64_t ndet, int64_t nsa, int64_t nsb, int npair_pad, int n_kc,
+                                                   int64_t n_blocks, const int32_t *__restrict__ pairA,
+                                                   const int32_t *__restrict__ pairB,
+                                                   const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
+    constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
+    const int row = threadIdx.x & 63, cc = threadIdx.x >> 6;
+    const uint32_t nsb32 = (uint32_t)nsb;
+    for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
+        const int64_t nt = blk / n_kc;
+        const int kc = (int)(blk - nt * n_kc);
+        const uint32_t det = (uint32_t)(nt * OZG_N + row);
+        const bool live = det < (uint64_t)ndet;
+        const uint32_t ka = live ? det / nsb32 : 0u, kb = live ? det - ka * nsb32 : 0u;
+        const int64_t *Crow = Cint + (int64_t)ka * nsb;
+        int32_t ea[8], eb[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int rs = kc * OZG_KC + cc * 8 + e;
+            const bool ok = live && rs < npair_pad;
+            ea[e] = ok ? __ldg(pairA + (int64_t)rs * nsa + ka) : -1;
+            eb[e] = ok ? __ldg(pairB + (int64_t)rs * nsb + kb) : -1;
+        }
+        uint32_t ylo[8], yhi[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int64_t xa = __ldg(Cint + (int64_t)(ea[e] >= 0 ? (ea[e] >> 1) : 0) * nsb + kb);
+            const int64_t xb = __ldg(Crow + (eb[e] >= 0 ? (eb[e] >> 1) : 0));
+            int64_t v = ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa : xa);
+            v += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb : xb);
+            const uint64_t y = (uint64_t)v + bias;
+            ylo[e] = (uint32_t)y;
+            yhi[e] = (uint32_t)(y >> 32);
+        }
+        uint8_t *base = Dimg + (size_t)blk * S * OZG_B_PLANE + ((row >> 3) * 4 + cc) * 128 + (row & 7) * 16;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            const uint32_t bj = (uint32_t)(j & 3), sel = bj | ((4u + bj) << 8);
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2)
+                w[e / 2] = j < 4 ? digits_f16x2(ylo[e], ylo[e + 1], sel) : digits_f16x2(yhi[e], yhi[e + 1], sel);
+            *(uint4 *)(base + j * OZG_B_PLANE) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+}
+
 inline size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 int oz_kc(const fci_context *h) { return ((h->npair + 15) / 16) * 2; }
@@ -455,6 +509,14 @@ int oz_ring(int s, int KC, int nt) {
 }
 // Tile width of this handle for s slices: the tuner's choice, else FCI_OZ_TILE from the
 // environment (32 or 64), else 64.
+// Contraction path for s slices: 1 = two-pass (digit image of D in HBM, then the
+// bulk-copy GEMM), 0 = fused producer kernel.  The tuner's choice, else FCI_OZ_PATH
+// ("gemm" / "fused") from the environment, else fused.
+int oz_path(const fci_context *h, int s) {
+    if (s >= 2 && s <= 8 && h->oz_tuned_nt[s]) return h->oz_tuned_path[s];
+    if (const char *env = getenv("FCI_OZ_PATH")) return strcmp(env, "gemm") == 0 ? 1 : 0;
+    return 0;
+}
 int oz_nt(const fci_context *h, int s) {
     if (s >= 2 && s <= 8 && h->oz_tuned_nt[s]) return h->oz_tuned_nt[s];
     if (const char *env = getenv("FCI_OZ_TILE")) {
@@ -519,10 +581,59 @@ int oz_prepare_G(fci_context *h, int s) {
     return FCI_OK;
 }
 
+// Two-pass path geometry: one M-tile of 128 pair rows, K = n_pair_pad rounded up to 32.
+static void oz_gemm_geom(const fci_context *h, int &n_kc, int64_t &n_nt) {
+    n_kc = (h->npair_pad + OZG_KC - 1) / OZG_KC;
+    n_nt = (h->ndet + OZG_N - 1) / OZG_N;
+}
+
+// Both paths' buffers fit (the tuner may switch between them): C_int, then either E_int of
+// the fused kernel or the D digit image + E_int of the two-pass path.
 size_t oz_workspace_bytes(const fci_context *h, int s) {
-    (void)s;
     const int64_t ntiles = (h->ndet + OZ_TILE - 1) / OZ_TILE;  // E for the widest tile covers the others
-    return al256((size_t)h->ndet * 8) + al256((size_t)ntiles * h->npair * OZ_TILE * 8) + 256;
+    const size_t fused = al256((size_t)ntiles * h->npair * OZ_TILE * 8);
+    int n_kc;
+    int64_t n_nt;
+    oz_gemm_geom(h, n_kc, n_nt);
+    const size_t two = al256((size_t)n_nt * n_kc * std::max(s, 2) * OZG_B_PLANE) + al256((size_t)n_nt * OZG_M * OZG_N * 8);
+    return al256((size_t)h->ndet * 8) + std::max(fused, two) + 256;
+}
+
+// G digit image in the A-tile layout of the bulk-copy GEMM ([K-chunk][plane][128 x 32]).
+static int oz_prepare_Gt(fci_context *h, int s) {
+    if (h->Gt_slices == s && h->d_Gt) return FCI_OK;
+    int rc = oz_prepare_G(h, s);  // checks, and sh_G
+    if (rc) return rc;
+    const int np = h->npair;
+    int n_kc;
+    int64_t n_nt;
+    oz_gemm_geom(h, n_kc, n_nt);
+    std::vector<double> G((size_t)np * np);
+    if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fci_cuda_check(h, cudaGetLastError(), "G download");
+    const int shG = h->G_exp;
+    uint64_t bias = 0;
+    for (int j = 0; j < s; ++j) bias |= (uint64_t)0x80 << (8 * j);
+    const size_t stageA = (size_t)s * OZG_A_PLANE;
+    std::vector<uint16_t> img((size_t)n_kc * stageA / 2, 0);
+    for (int m = 0; m < OZG_M; ++m)
+        for (int k = 0; k < n_kc * OZG_KC; ++k) {
+            int64_t gi = 0;
+            if (m < np && k < np) gi = llrint(ldexp(G[(size_t)m * np + k], shG));
+            const uint64_t y = (uint64_t)gi + bias;
+            const int kc = k / OZG_KC, kk = k % OZG_KC;
+            const size_t off = (size_t)kc * stageA + ((m >> 3) * 4 + (kk >> 3)) * 128 + (m & 7) * 16 + (kk & 7) * 2;
+            for (int j = 0; j < s; ++j)
+                img[(off + (size_t)j * OZG_A_PLANE) / 2] = half_bits_of_small_int((int)((y >> (8 * j)) & 0xFF) - 128);
+        }
+    fci_dev_free(h->d_Gt);
+    h->d_Gt = nullptr;
+    h->Gt_slices = 0;
+    rc = fci_dev_alloc(h, &h->d_Gt, img.size() * 2);
+    if (rc) return rc;
+    FCI_CUDA(h, cudaMemcpy(h->d_Gt, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
+    h->Gt_slices = s;
+    return FCI_OK;
 }
 
 // Fixed-point conversion of C and the job's kernel parameters (first half of a split sigma).
@@ -606,7 +717,8 @@ static int oz_finish_job(fci_context *h, const double *C, double *sigma, const O
     phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
     const int threads = 128;
     dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
-    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, prm.nt == 32 ? 5 : 6, h->d_pair_a, h->d_pair_b, E, 0,
+    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, prm.nt == 32 ? 5 : 6, h->d_pair_a, h->d_pair_b, E,
+                                       prm.npair,
                                        C, h->e_core,
                                        8 * prm.L0 - h->G_exp, shC, status, sigma);
     FCI_CUDA(h, cudaGetLastError());
@@ -618,8 +730,71 @@ static int oz_num_sms(fci_context *h, int *nsm) {
     return FCI_OK;
 }
 
+// Two-pass split sigma: fixed point, D digit image (k_fci_split), bulk-copy GEMM (8-bit
+// digits, one M-tile of 128 pair rows), integer scatter.
+static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int s, void *ws, cudaStream_t st) {
+    int rc = oz_prepare_Gt(h, s);
+    if (rc) return rc;
+    if (!oz_gemm_ring(s)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit the GEMM pipeline", s);
+    int n_kc;
+    int64_t n_nt;
+    oz_gemm_geom(h, n_kc, n_nt);
+    const int64_t N = h->ndet;
+    char *p = (char *)ws;
+    int64_t *Cint = (int64_t *)p;
+    p += al256((size_t)N * 8);
+    uint8_t *Dimg = (uint8_t *)p;
+    p += al256((size_t)n_nt * n_kc * s * OZG_B_PLANE);
+    int64_t *E = (int64_t *)p;
+    p += al256((size_t)n_nt * OZG_M * OZG_N * 8);
+    // the misc block sits at the end of the larger of the two layouts
+    char *misc = (char *)ws + (oz_workspace_bytes(h, s) - 256);
+    unsigned long long *maxbits = (unsigned long long *)misc;
+    int *shC = (int *)(misc + 8), *status = (int *)(misc + 16);
+    h->last_status = status;
+    {
+        phase_scope ps(h, st, FCI_PHASE_GATHER, 3);
+        FCI_CUDA(h, cudaMemsetAsync(misc, 0, 256, st));
+        const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(N, 256), 152 * 8);
+        k_absmax_bits<<<nb, 256, 0, st>>>(C, N, maxbits);
+        k_to_fixed<<<nb, 256, 0, st>>>(C, N, s, maxbits, Cint, shC);
+        const int64_t nblk = n_nt * n_kc;
+        const unsigned gb = (unsigned)std::min<int64_t>(nblk, 152 * 16);
+        switch (s) {
+#define OZ_SPLIT(S_)                                                                                           \
+    case S_:                                                                                                   \
+        k_fci_split<S_><<<gb, 256, 0, st>>>(N, h->nsa, h->nsb, h->npair_pad, n_kc, nblk, h->d_pair_a, h->d_pair_b, \
+                                            Cint, Dimg);                                                       \
+        break;
+            OZ_SPLIT(2) OZ_SPLIT(3) OZ_SPLIT(4) OZ_SPLIT(5) OZ_SPLIT(6) OZ_SPLIT(7)
+#undef OZ_SPLIT
+            default: return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d", s);
+        }
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    oz_gemm_args a;
+    a.n_mt = 1;
+    a.n_kc = n_kc;
+    a.M_pad = OZG_M;
+    a.M_real = h->npair;
+    a.n_nt = n_nt;
+    a.Gimg = h->d_Gt;
+    a.Dimg = Dimg;
+    a.E = E;
+    a.status = status;
+    if ((rc = oz_gemm_launch(h, s, 8, a, st))) return rc;
+    phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
+    const int threads = 128;
+    dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
+    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, 6, h->d_pair_a, h->d_pair_b, E, OZG_M, C,
+                                       h->e_core, 8 * oz_gemm_L0(s, 8) - h->G_exp, shC, status, sigma);
+    FCI_CUDA(h, cudaGetLastError());
+    return FCI_OK;
+}
+
 int oz_sigma_fci(fci_context *h, const double *C, double *sigma, int s, void *ws, size_t ws_bytes, cudaStream_t st) {
     (void)ws_bytes;
+    if (oz_path(h, s) == 1) return oz_sigma_fci_gemm(h, C, sigma, s, ws, st);
     OzGroup grp;
     int64_t *E;
     int *shC, *status;
@@ -684,16 +859,22 @@ static int oz_sigma_group_nt(fci_context *const *hs, const double *const *Cs, do
     return FCI_OK;
 }
 
-// Jobs grouped by their tile width (the kernel's template argument), one launch per group.
+// Jobs grouped by their tile width (the kernel's template argument), one launch per group;
+// jobs configured for the two-pass path run one after another.
 int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *const *sigmas, void *const *wss, int n,
                    int s, cudaStream_t st) {
+    for (int i = 0; i < n; ++i)
+        if (oz_path(hs[i], s) == 1) {
+            const int rc = oz_sigma_fci_gemm(hs[i], Cs[i], sigmas[i], s, wss[i], st);
+            if (rc) return rc;
+        }
     for (int nt : {64, 32}) {
         std::vector<fci_context *> h2;
         std::vector<const double *> c2;
         std::vector<double *> s2;
         std::vector<void *> w2;
         for (int i = 0; i < n; ++i)
-            if (oz_nt(hs[i], s) == nt) {
+            if (oz_path(hs[i], s) == 0 && oz_nt(hs[i], s) == nt) {
                 h2.push_back(hs[i]);
                 c2.push_back(Cs[i]);
                 s2.push_back(sigmas[i]);
@@ -706,14 +887,24 @@ int oz_sigma_group(fci_context *const *hs, const double *const *Cs, double *cons
     return FCI_OK;
 }
 
-int oz_tune_candidates(const fci_context *h, int s, int *nt, int max) {
+int oz_tune_candidates(const fci_context *h, int s, int *nt, int *path, int max) {
     const int KC = oz_kc(h);
     int n = 0;
     for (int t : {64, 32})
-        if (n < max && s * t <= 512 && oz_ring(s, KC, t)) nt[n++] = t;
+        if (n < max && s * t <= 512 && oz_ring(s, KC, t)) {
+            nt[n] = t;
+            path[n++] = 0;
+        }
+    if (n < max && s <= 7 && oz_gemm_ring(s)) {  // two-pass: 64-determinant tiles
+        nt[n] = 64;
+        path[n++] = 1;
+    }
     return n;
 }
 
-void oz_set_config(fci_context *h, int s, int nt) {
-    if (s >= 2 && s <= 8) h->oz_tuned_nt[s] = nt;
+void oz_set_config(fci_context *h, int s, int nt, int path) {
+    if (s >= 2 && s <= 8) {
+        h->oz_tuned_nt[s] = nt;
+        h->oz_tuned_path[s] = nt ? path : 0;
+    }
 }

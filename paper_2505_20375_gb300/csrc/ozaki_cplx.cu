@@ -18,14 +18,7 @@
 // away), and the scatter sums in int64:
 //   sigma_I = 2^{7 L0 - sh_G - sh_C} sum <I|E_x|K> E_int[x, K] + e_core C_I.
 //
-// Kernel layout (one persistent CTA per SM, 192 threads):
-//   warp 0  lane 0 issues the bulk copies of each stage (G tile: s planes of 128 x 32,
-//           D tile: s planes of 64 x 32, f16 core matrices);
-//   warp 1  allocates TMEM; lane 0 issues the MMAs (M = 128, N = 64, K = 16) and commits;
-//   warps 2-5 epilogue, one per TMEM lane quadrant.
-// Work units are (N-tile, M-tile) pairs, N-tile outer and dealt round-robin, so the
-// M-tiles of one D tile run at the same time and its reads hit L2.  All mbarrier waits
-// are bounded in time (FCI_ERR_TIMEOUT in the status word on expiry).
+// The GEMM itself is the shared bulk-copy kernel (ozaki_gemm.cu) with 7-bit digits.
 #include <math.h>
 #include <stdlib.h>
 
@@ -34,243 +27,19 @@
 #include <vector>
 
 #include "fci_internal.h"
+#include "oz_gemm.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
 
 using namespace tc;
 
-constexpr int CZ_M = 128;   // rows of G per tile
-constexpr int CZ_N = 64;    // determinants per tile
-constexpr int CZ_KC = 32;   // K per pipeline stage (4 core matrices of 8)
-constexpr int CZ_THREADS = 192;
-constexpr int CZ_MAX_STAGES = 6;
-constexpr int CZ_A_PLANE = CZ_M * CZ_KC * 2;  // 8 KB
-constexpr int CZ_B_PLANE = CZ_N * CZ_KC * 2;  // 4 KB
-constexpr size_t CZ_SMEM_MAX = 232448 - 1024;
-constexpr int CZ_MAXS = 8;
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-struct CzParams {
-    int n_mt, n_kc, M_pad, ring;
-    int64_t n_nt;
-    const uint8_t *Gimg, *Dimg;
-    int64_t *E;
-    int *status;
-    long long timeout_cycles;
-};
-
-struct CzShared {
-    uint64_t full[CZ_MAX_STAGES], empty[CZ_MAX_STAGES];
-    uint64_t acc_full[2], acc_empty[2];
-    uint64_t drain;
-    uint32_t tmem_base;
-    int abort;
-};
-
-__device__ __forceinline__ bool cz_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
-                                        long long timeout) {
-    const long long t0 = clock64();
-    int spins = 0;
-    while (!mbar_try_wait_sleep(bar, parity)) {
-        if (((++spins) & 3) == 0) {
-            if (*abort) return false;
-            if (clock64() - t0 > timeout) {
-                *abort = 1;
-                atomicExch(status, FCI_ERR_TIMEOUT);
-                return false;
-            }
-        }
-    }
-    return true;
-}
-
-__device__ __forceinline__ bool cz_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
-                                             long long timeout) {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = cz_wait(bar, parity, abort, status, timeout) ? 1 : 0;
-    return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
-}
-
-template <int S>
-__global__ void __launch_bounds__(CZ_THREADS, 1) k_cz_gemm(const __grid_constant__ CzParams p) {
-    constexpr int NBUF = (2 * S * CZ_N <= 512) ? 2 : 1;
-    constexpr int L0 = (S - 1 > 2 * S - 7) ? S - 1 : 2 * S - 7;
-    constexpr uint32_t STAGE_A = S * CZ_A_PLANE, STAGE_B = S * CZ_B_PLANE;
-    extern __shared__ __align__(1024) uint8_t cz_smem_raw[];
-    uint8_t *smem = (uint8_t *)(((uintptr_t)cz_smem_raw + 1023) & ~(uintptr_t)1023);
-    const int R = p.ring;
-    uint8_t *sA = smem;                              // R stages of S A-planes
-    uint8_t *sB = sA + (size_t)R * STAGE_A;          // R stages of S B-planes
-    CzShared *sh = (CzShared *)(sB + (size_t)R * STAGE_B);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int r = 0; r < R; ++r) {
-            mbar_init(smem_u32(&sh->full[r]), 1);
-            mbar_init(smem_u32(&sh->empty[r]), 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&sh->acc_full[b]), 1);
-            mbar_init(smem_u32(&sh->acc_empty[b]), 4);
-        }
-        mbar_init(smem_u32(&sh->drain), 1);
-        sh->abort = 0;
-        fence_barrier_init();
-    }
-    if (warp == 1) {
-        tmem_alloc(smem_u32(&sh->tmem_base), 512);
-        tmem_relinquish();
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = sh->tmem_base;
-    volatile int *abort = &sh->abort;
-    const int64_t n_units = p.n_nt * p.n_mt;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            // ------------------------------------------------------------ bulk copies
-            uint32_t q = 0;
-            for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
-                const int64_t nt = u / p.n_mt;
-                const int mt = (int)(u - nt * p.n_mt);
-                const uint8_t *ga = p.Gimg + (size_t)mt * p.n_kc * STAGE_A;
-                const uint8_t *gb = p.Dimg + (size_t)nt * p.n_kc * STAGE_B;
-                bool ok = true;
-                for (int kc = 0; kc < p.n_kc; ++kc, ++q) {
-                    const int st = (int)(q % (uint32_t)R);
-                    const uint32_t use = q / (uint32_t)R;
-                    if (use > 0 && !cz_wait(smem_u32(&sh->empty[st]), (use - 1) & 1, abort, p.status,
-                                            p.timeout_cycles)) {
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t fb = smem_u32(&sh->full[st]);
-                    mbar_expect_tx(fb, STAGE_A + STAGE_B);
-                    bulk_g2s(smem_u32(sA + (size_t)st * STAGE_A), ga + (size_t)kc * STAGE_A, STAGE_A, fb);
-                    bulk_g2s(smem_u32(sB + (size_t)st * STAGE_B), gb + (size_t)kc * STAGE_B, STAGE_B, fb);
-                }
-                if (!ok) break;
-            }
-        }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            // ------------------------------------------------------------ MMA issuer
-            const uint32_t idesc = idesc_f16(CZ_M, CZ_N);
-            const uint64_t a0 = smem_desc(smem_u32(sA), 128, 4 * 128);
-            const uint64_t b0 = smem_desc(smem_u32(sB), 128, 4 * 128);
-            uint32_t q = 0, tau = 0;
-            bool issued = false, ok = true;
-            for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++tau) {
-                const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
-                if (tau >= (uint32_t)NBUF) {
-                    const uint32_t par = NBUF == 2 ? ((tau >> 1) - 1) & 1 : (tau - 1) & 1;
-                    if (!cz_wait(smem_u32(&sh->acc_empty[buf]), par, abort, p.status, p.timeout_cycles)) break;
-                }
-                tc_fence_after();
-                const uint32_t dbase = tmem + (uint32_t)(buf * S * CZ_N);
-                for (int kc = 0; kc < p.n_kc; ++kc, ++q) {
-                    const int st = (int)(q % (uint32_t)R);
-                    if (!cz_wait(smem_u32(&sh->full[st]), (q / (uint32_t)R) & 1, abort, p.status, p.timeout_cycles)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint64_t as = a0 + (uint64_t)((st * STAGE_A) >> 4);
-                    const uint64_t bs = b0 + (uint64_t)((st * STAGE_B) >> 4);
-#pragma unroll
-                    for (int kk = 0; kk < CZ_KC / 16; ++kk) {
-#pragma unroll
-                        for (int j = S - 1; j >= 0; --j) {
-                            const uint64_t b = bs + (uint64_t)((j * CZ_B_PLANE + kk * 256) >> 4);
-                            const uint32_t acc_in = (kc != 0 || kk != 0 || j != S - 1) ? 1u : 0u;
-#pragma unroll
-                            for (int i = S - 1 - j; i < S; ++i)
-                                mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * CZ_N),
-                                        as + (uint64_t)((i * CZ_A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
-                        }
-                    }
-                    issued = true;
-                    mma_commit(smem_u32(&sh->empty[st]));
-                }
-                if (!ok) break;
-                mma_commit(smem_u32(&sh->acc_full[buf]));
-            }
-            if (issued) {
-                mma_commit(smem_u32(&sh->drain));
-                const long long t0 = clock64();
-                while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
-                    if (clock64() - t0 > p.timeout_cycles) {
-                        atomicExch(p.status, FCI_ERR_TIMEOUT);
-                        break;
-                    }
-                }
-            }
-        }
-    } else {
-        // ---------------------------------------------------------------- epilogue
-        const int qd = warp & 3;
-        const int row = 32 * qd + lane;
-        constexpr int lowshift = 7 * (L0 - (S - 1));
-        uint32_t tau = 0;
-        for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++tau) {
-            const int64_t nt = u / p.n_mt;
-            const int mt = (int)(u - nt * p.n_mt);
-            const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
-            const uint32_t par = NBUF == 2 ? (tau >> 1) & 1 : tau & 1;
-            if (!cz_wait_warp(smem_u32(&sh->acc_full[buf]), par, abort, p.status, p.timeout_cycles)) break;
-            tc_fence_after();
-            const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * CZ_N);
-            int64_t *dst_row = p.E + ((size_t)nt * p.M_pad + (size_t)mt * CZ_M + row) * CZ_N;
-#pragma unroll 1
-            for (int c0 = 0; c0 < CZ_N; c0 += 16) {
-                int64_t acc[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) acc[c] = 0;
-#pragma unroll
-                for (int L = S - 1; L <= 2 * S - 2; ++L) {
-                    uint32_t v[16];
-                    tmem_ld16(tl + (uint32_t)((L - (S - 1)) * CZ_N + c0), v);
-                    tmem_ld_wait();
-                    if (L < L0) {
-#pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (7 * (L - (S - 1))));
-                    } else {
-                        if (L == L0 && lowshift > 0) {
-#pragma unroll
-                            for (int c = 0; c < 16; ++c)
-                                acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
-                        }
-#pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (7 * (L - L0)));
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 16; c += 2) __stcs((longlong2 *)(dst_row + c0 + c), make_longlong2(acc[c], acc[c + 1]));
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, 512);
-}
+constexpr int CZ_M = OZG_M;
+constexpr int CZ_N = OZG_N;
+constexpr int CZ_KC = OZG_KC;
+constexpr int CZ_A_PLANE = OZG_A_PLANE;
+constexpr int CZ_B_PLANE = OZG_B_PLANE;
+constexpr int CZ_MAXS = OZG_MAXS;
 
 // ------------------------------------------------------------- helper kernels
 
@@ -421,12 +190,11 @@ uint16_t half_bits_of_small_int(int d) {  // IEEE binary16 of an integer |d| <= 
 }
 
 struct CzGeom {
-    int M_real, M_pad, K_pad, n_mt, n_kc, ring;
+    int M_real, M_pad, K_pad, n_mt, n_kc;
     int64_t n_nt;
-    size_t smem;
 };
 
-void cz_geom(const fci_context *h, int s, CzGeom &g) {
+void cz_geom(const fci_context *h, CzGeom &g) {
     const int n2 = h->n_orb * h->n_orb;
     g.M_real = 2 * n2;
     g.M_pad = (g.M_real + CZ_M - 1) / CZ_M * CZ_M;
@@ -434,19 +202,7 @@ void cz_geom(const fci_context *h, int s, CzGeom &g) {
     g.n_mt = g.M_pad / CZ_M;
     g.n_kc = g.K_pad / CZ_KC;
     g.n_nt = (h->ndet + CZ_N - 1) / CZ_N;
-    const size_t stage = (size_t)s * (CZ_A_PLANE + CZ_B_PLANE);
-    const size_t fixed = 1024 + sizeof(CzShared) + 64;
-    g.ring = (int)std::min<size_t>(CZ_MAX_STAGES, (CZ_SMEM_MAX - fixed) / stage);
-    g.smem = fixed + (size_t)g.ring * stage;
 }
-
-int cz_num_sms(fci_context *h, int *nsm) {
-    FCI_CUDA(h, cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, h->device));
-    return FCI_OK;
-}
-
-template <int S>
-void (*cz_gemm_kernel())(const CzParams) { return k_cz_gemm<S>; }
 
 }  // namespace
 
@@ -458,9 +214,7 @@ int cz_check(fci_context *h, int s) {
     if ((int64_t)s * nnz * 4096 >= ((int64_t)1 << 24))
         return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices x %lld nonzero terms could exceed 2^24 in a level sum", s,
                         (long long)nnz);
-    CzGeom g;
-    cz_geom(h, s, g);
-    if (g.ring < 2) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit two pipeline stages", s);
+    if (!oz_gemm_ring(s)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit two pipeline stages", s);
     return FCI_OK;
 }
 
@@ -468,7 +222,7 @@ int cz_check(fci_context *h, int s) {
 static int cz_prepare_G(fci_context *h, int s) {
     if (h->Gs_slices == s && h->d_Gs) return FCI_OK;
     CzGeom g;
-    cz_geom(h, s, g);
+    cz_geom(h, g);
     const int n2 = h->n_orb * h->n_orb;
     std::vector<double> G((size_t)n2 * n2 * 2);
     if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -513,7 +267,7 @@ static int cz_prepare_G(fci_context *h, int s) {
 
 size_t cz_workspace_bytes(const fci_context *h, int s) {
     CzGeom g;
-    cz_geom(h, s < 2 ? 2 : s, g);
+    cz_geom(h, g);
     return al256((size_t)h->ndet * 16) + al256((size_t)g.n_nt * g.n_kc * s * CZ_B_PLANE) +
            al256((size_t)g.n_nt * g.M_pad * CZ_N * 8) + 256;
 }
@@ -524,7 +278,7 @@ int cz_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, si
     if (!rc) rc = cz_prepare_G(h, s);
     if (rc) return rc;
     CzGeom g;
-    cz_geom(h, s, g);
+    cz_geom(h, g);
     char *p = (char *)ws;
     int64_t *Cint = (int64_t *)p;
     p += al256((size_t)h->ndet * 16);
@@ -551,39 +305,21 @@ int cz_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, si
         FCI_CUDA(h, cudaGetLastError());
     }
     {
-        void (*kern)(const CzParams) = nullptr;
-        switch (s) {
-            case 2: kern = cz_gemm_kernel<2>(); break;
-            case 3: kern = cz_gemm_kernel<3>(); break;
-            case 4: kern = cz_gemm_kernel<4>(); break;
-            case 5: kern = cz_gemm_kernel<5>(); break;
-            case 6: kern = cz_gemm_kernel<6>(); break;
-            case 7: kern = cz_gemm_kernel<7>(); break;
-            case 8: kern = cz_gemm_kernel<8>(); break;
-        }
-        CzParams prm;
-        prm.n_mt = g.n_mt;
-        prm.n_kc = g.n_kc;
-        prm.M_pad = g.M_pad;
-        prm.ring = g.ring;
-        prm.n_nt = g.n_nt;
-        prm.Gimg = (const uint8_t *)h->d_Gs;
-        prm.Dimg = Dimg;
-        prm.E = E;
-        prm.status = status;
-        const char *to = getenv("FCI_WAIT_TIMEOUT_MS");
-        prm.timeout_cycles = (long long)((to ? atof(to) : 2000.0) * 2.1e6);
-        int nsm = 0;
-        if ((rc = cz_num_sms(h, &nsm))) return rc;
-        const int64_t units = g.n_nt * g.n_mt;
-        FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
-        phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
-        kern<<<(unsigned)std::min<int64_t>(nsm, units), CZ_THREADS, g.smem, st>>>(prm);
-        FCI_CUDA(h, cudaGetLastError());
+        oz_gemm_args a;
+        a.n_mt = g.n_mt;
+        a.n_kc = g.n_kc;
+        a.M_pad = g.M_pad;
+        a.M_real = g.M_real;
+        a.n_nt = g.n_nt;
+        a.Gimg = h->d_Gs;
+        a.Dimg = Dimg;
+        a.E = E;
+        a.status = status;
+        if ((rc = oz_gemm_launch(h, s, 7, a, st))) return rc;
     }
     {
         phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
-        const int L0 = std::max(s - 1, 2 * s - 7);
+        const int L0 = oz_gemm_L0(s, 7);
         k_cz_scatter<<<(unsigned)ceil_div(h->ndet, 128), 128, 0, st>>>(h->n_orb, h->ndet, g.M_pad, h->d_str_a,
                                                                         h->d_binom, E, C, h->e_core,
                                                                         7 * L0 - h->G_exp, shC, status, sigma);

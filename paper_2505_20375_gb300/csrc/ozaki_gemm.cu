@@ -1,0 +1,305 @@
+// Kernel layout (one persistent CTA per SM, 320 threads):
+//   warp 0     lane 0 issues the two bulk copies of each pipeline stage (A tile: s planes
+//              of 128 x 32, B tile: s planes of 64 x 32), completing on the stage's mbarrier;
+//   warp 1     allocates TMEM; lane 0 issues the MMAs (M = 128, N = 64, K = 16) into the
+//              s level accumulators and commits;
+//   warps 2-9  epilogue, two per TMEM lane quadrant (32 columns each).
+// Level accumulators are double-buffered when 2 s x 64 TMEM columns fit in 512.  Work units
+// are (N-tile, M-tile) pairs, N-tile outer and dealt round-robin, so the M-tiles of one
+// B tile run at about the same time and its reads hit L2.  Every mbarrier wait is bounded
+// in time (FCI_ERR_TIMEOUT in the status word on expiry; the kernel drains the MMAs it
+// issued and frees TMEM before returning).
+#include <stdlib.h>
+
+#include <algorithm>
+
+#include "oz_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+using namespace tc;
+
+constexpr int OZG_EPI_WARPS = 8;  // two per TMEM lane quadrant, 32 columns each
+constexpr int OZG_THREADS = 32 * (2 + OZG_EPI_WARPS);  // 320
+constexpr int OZG_MAX_STAGES = 6;
+constexpr size_t OZG_SMEM_MAX = 232448 - 1024;
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+struct OzgParams {
+    int n_mt, n_kc, M_pad, M_real, ring;
+    int64_t n_nt;
+    const uint8_t *Gimg, *Dimg;
+    int64_t *E;
+    int *status;
+    long long timeout_cycles;
+};
+
+struct OzgShared {
+    uint64_t full[OZG_MAX_STAGES], empty[OZG_MAX_STAGES];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t drain;
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ __forceinline__ bool ozg_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                        long long timeout) {
+    const long long t0 = clock64();
+    int spins = 0;
+    while (!mbar_try_wait_sleep(bar, parity)) {
+        if (((++spins) & 3) == 0) {
+            if (*abort) return false;
+            if (clock64() - t0 > timeout) {
+                *abort = 1;
+                atomicExch(status, FCI_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool ozg_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
+                                             long long timeout) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = ozg_wait(bar, parity, abort, status, timeout) ? 1 : 0;
+    return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
+}
+
+template <int S, int W>
+__global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constant__ OzgParams p) {
+    constexpr int NBUF = (2 * S * OZG_N <= 512) ? 2 : 1;
+    constexpr int L0 = oz_gemm_L0(S, W);
+    constexpr uint32_t STAGE_A = S * OZG_A_PLANE, STAGE_B = S * OZG_B_PLANE;
+    extern __shared__ __align__(1024) uint8_t cz_smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)cz_smem_raw + 1023) & ~(uintptr_t)1023);
+    const int R = p.ring;
+    uint8_t *sA = smem;                              // R stages of S A-planes
+    uint8_t *sB = sA + (size_t)R * STAGE_A;          // R stages of S B-planes
+    OzgShared *sh = (OzgShared *)(sB + (size_t)R * STAGE_B);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < R; ++r) {
+            mbar_init(smem_u32(&sh->full[r]), 1);
+            mbar_init(smem_u32(&sh->empty[r]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&sh->acc_full[b]), 1);
+            mbar_init(smem_u32(&sh->acc_empty[b]), OZG_EPI_WARPS);
+        }
+        mbar_init(smem_u32(&sh->drain), 1);
+        sh->abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(smem_u32(&sh->tmem_base), 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+    volatile int *abort = &sh->abort;
+    const int64_t n_units = p.n_nt * p.n_mt;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ bulk copies
+            uint32_t q = 0;
+            for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
+                const int64_t nt = u / p.n_mt;
+                const int mt = (int)(u - nt * p.n_mt);
+                const uint8_t *ga = p.Gimg + (size_t)mt * p.n_kc * STAGE_A;
+                const uint8_t *gb = p.Dimg + (size_t)nt * p.n_kc * STAGE_B;
+                bool ok = true;
+                for (int kc = 0; kc < p.n_kc; ++kc, ++q) {
+                    const int st = (int)(q % (uint32_t)R);
+                    const uint32_t use = q / (uint32_t)R;
+                    if (use > 0 && !ozg_wait(smem_u32(&sh->empty[st]), (use - 1) & 1, abort, p.status,
+                                            p.timeout_cycles)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&sh->full[st]);
+                    mbar_expect_tx(fb, STAGE_A + STAGE_B);
+                    bulk_g2s(smem_u32(sA + (size_t)st * STAGE_A), ga + (size_t)kc * STAGE_A, STAGE_A, fb);
+                    bulk_g2s(smem_u32(sB + (size_t)st * STAGE_B), gb + (size_t)kc * STAGE_B, STAGE_B, fb);
+                }
+                if (!ok) break;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------------------------------------ MMA issuer
+            const uint32_t idesc = idesc_f16(OZG_M, OZG_N);
+            const uint64_t a0 = smem_desc(smem_u32(sA), 128, 4 * 128);
+            const uint64_t b0 = smem_desc(smem_u32(sB), 128, 4 * 128);
+            uint32_t q = 0, tau = 0;
+            bool issued = false, ok = true;
+            for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++tau) {
+                const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
+                if (tau >= (uint32_t)NBUF) {
+                    const uint32_t par = NBUF == 2 ? ((tau >> 1) - 1) & 1 : (tau - 1) & 1;
+                    if (!ozg_wait(smem_u32(&sh->acc_empty[buf]), par, abort, p.status, p.timeout_cycles)) break;
+                }
+                tc_fence_after();
+                const uint32_t dbase = tmem + (uint32_t)(buf * S * OZG_N);
+                for (int kc = 0; kc < p.n_kc; ++kc, ++q) {
+                    const int st = (int)(q % (uint32_t)R);
+                    if (!ozg_wait(smem_u32(&sh->full[st]), (q / (uint32_t)R) & 1, abort, p.status, p.timeout_cycles)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t as = a0 + (uint64_t)((st * STAGE_A) >> 4);
+                    const uint64_t bs = b0 + (uint64_t)((st * STAGE_B) >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < OZG_KC / 16; ++kk) {
+#pragma unroll
+                        for (int j = S - 1; j >= 0; --j) {
+                            const uint64_t b = bs + (uint64_t)((j * OZG_B_PLANE + kk * 256) >> 4);
+                            const uint32_t acc_in = (kc != 0 || kk != 0 || j != S - 1) ? 1u : 0u;
+#pragma unroll
+                            for (int i = S - 1 - j; i < S; ++i)
+                                mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * OZG_N),
+                                        as + (uint64_t)((i * OZG_A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
+                        }
+                    }
+                    issued = true;
+                    mma_commit(smem_u32(&sh->empty[st]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&sh->acc_full[buf]));
+            }
+            if (issued) {
+                mma_commit(smem_u32(&sh->drain));
+                const long long t0 = clock64();
+                while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
+                    if (clock64() - t0 > p.timeout_cycles) {
+                        atomicExch(p.status, FCI_ERR_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- epilogue
+        const int qd = warp & 3;
+        const int cbeg = (OZG_N / 2) * ((warp - 2) >> 2);  // this warp's half of the columns
+        const int row = 32 * qd + lane;
+        constexpr int lowshift = W * (L0 - (S - 1));
+        uint32_t tau = 0;
+        for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++tau) {
+            const int64_t nt = u / p.n_mt;
+            const int mt = (int)(u - nt * p.n_mt);
+            const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
+            const uint32_t par = NBUF == 2 ? (tau >> 1) & 1 : tau & 1;
+            if (!ozg_wait_warp(smem_u32(&sh->acc_full[buf]), par, abort, p.status, p.timeout_cycles)) break;
+            tc_fence_after();
+            const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * OZG_N);
+            int64_t *dst_row = p.E + ((size_t)nt * p.M_pad + (size_t)mt * OZG_M + row) * OZG_N;
+#pragma unroll 1
+            for (int c0 = cbeg; c0 < cbeg + OZG_N / 2; c0 += 16) {
+                int64_t acc[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) acc[c] = 0;
+#pragma unroll
+                for (int L = S - 1; L <= 2 * S - 2; ++L) {
+                    uint32_t v[16];
+                    tmem_ld16(tl + (uint32_t)((L - (S - 1)) * OZG_N + c0), v);
+                    tmem_ld_wait();
+                    if (L < L0) {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - (S - 1))));
+                    } else {
+                        if (L == L0 && lowshift > 0) {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
+                        }
+#pragma unroll
+                        for (int c = 0; c < 16; ++c)
+                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - L0)));
+                    }
+                }
+#pragma unroll
+                if (mt * OZG_M + row < p.M_real)  // rows past the operator's size are never read
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2)
+                        __stcs((longlong2 *)(dst_row + c0 + c), make_longlong2(acc[c], acc[c + 1]));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, 512);
+}
+
+
+template <int W>
+void (*oz_gemm_kernel(int s))(const OzgParams) {
+    switch (s) {
+        case 2: return k_oz_gemm<2, W>;
+        case 3: return k_oz_gemm<3, W>;
+        case 4: return k_oz_gemm<4, W>;
+        case 5: return k_oz_gemm<5, W>;
+        case 6: return k_oz_gemm<6, W>;
+        case 7: return k_oz_gemm<7, W>;
+        case 8: return k_oz_gemm<8, W>;
+        default: return nullptr;
+    }
+}
+
+size_t oz_gemm_fixed() { return 1024 + sizeof(OzgShared) + 64; }
+
+}  // namespace
+
+int oz_gemm_ring(int s) {
+    const size_t stage = (size_t)s * (OZG_A_PLANE + OZG_B_PLANE);
+    const size_t r = (OZG_SMEM_MAX - oz_gemm_fixed()) / stage;
+    return r < 2 ? 0 : (int)std::min<size_t>(OZG_MAX_STAGES, r);
+}
+
+int oz_gemm_launch(fci_context *h, int s, int w, const oz_gemm_args &a, cudaStream_t st) {
+    void (*kern)(const OzgParams) = w == 7 ? oz_gemm_kernel<7>(s) : w == 8 ? oz_gemm_kernel<8>(s) : nullptr;
+    const int ring = oz_gemm_ring(s);
+    if (!kern || !ring) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split GEMM: %d slices of %d bits", s, w);
+    OzgParams prm;
+    prm.n_mt = a.n_mt;
+    prm.n_kc = a.n_kc;
+    prm.M_pad = a.M_pad;
+    prm.M_real = a.M_real;
+    prm.ring = ring;
+    prm.n_nt = a.n_nt;
+    prm.Gimg = (const uint8_t *)a.Gimg;
+    prm.Dimg = (const uint8_t *)a.Dimg;
+    prm.E = a.E;
+    prm.status = a.status;
+    const char *to = getenv("FCI_WAIT_TIMEOUT_MS");
+    prm.timeout_cycles = (long long)((to ? atof(to) : 2000.0) * 2.1e6);
+    int nsm = 0;
+    FCI_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
+    const size_t smem = oz_gemm_fixed() + (size_t)ring * s * (OZG_A_PLANE + OZG_B_PLANE);
+    FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t units = a.n_nt * a.n_mt;
+    phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
+    kern<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm, units)), OZG_THREADS, smem, st>>>(prm);
+    FCI_CUDA(h, cudaGetLastError());
+    return FCI_OK;
+}

@@ -284,7 +284,8 @@ class FCI:
                           ctypes.byref(r)))
         das = bool(self.info["n_categories"])
         cands = [({"k_chunk_cores": r.param_a[i], "producer_warps": r.param_b[i]} if das
-                  else {"dets_per_tile": r.param_a[i]}) | {"ms": r.ms[i]} for i in range(r.n_candidates)]
+                  else {"dets_per_tile": r.param_a[i], "path": "two-pass gemm" if r.param_b[i] else "fused"})
+                 | {"ms": r.ms[i]} for i in range(r.n_candidates)]
         return {"n_slices": n_slices, "candidates": cands, "chosen": cands[r.chosen]}
 
     def davidson_opts(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
