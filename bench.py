@@ -279,6 +279,13 @@ def run_ours(a, rank, world, local_rank):
     davidson = None
     if not a.no_davidson and rank == 0:
         davidson = {}
+        tuned_dav = {}
+        for s_t in (3, 7):  # tile shape of each slice count the forms use (untimed setup)
+            try:
+                tuned_dav[f"s{s_t}"] = f.tune(C, s_t, reps=2)["chosen"]
+            except fci.FCIError as e:
+                tuned_dav[f"s{s_t}"] = {"unavailable": str(e)[:200]}
+        davidson["autotune"] = tuned_dav
         forms = (("fp64", dict(precision="fp64")),
                  ("oz_s7", dict(precision="oz_bf16", n_slices=7, final_precision="oz_bf16", final_slices=7)),
                  ("mixed_s3_then_oz_s7", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4,
@@ -298,7 +305,7 @@ def run_ours(a, rank, world, local_rank):
                 davidson[name] = {"unavailable": str(e)[:200]}
         e64 = davidson.get("fp64", {}).get("energy")
         for name, d in davidson.items():
-            if e64 is not None and "energy" in d and name != "fp64":
+            if e64 is not None and isinstance(d, dict) and "energy" in d and name != "fp64":
                 d["energy_error_vs_fp64"] = abs(d["energy"] - e64)
                 d["speedup_vs_fp64"] = davidson["fp64"]["seconds"] / d["seconds"]
 
