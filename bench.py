@@ -53,6 +53,11 @@ def _args():
                     help="requests of the serving run (0 = skip); 256 is the full request stream")
     ap.add_argument("--serving-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--no-configs", action="store_true", help="skip the single-sigma runs of the other configs")
+    ap.add_argument("--profile-case", default=None,
+                    help="only run --steps sigma builds of this workload (a profiling target) and exit")
+    ap.add_argument("--path", default=None, choices=["fused", "gemm"],
+                    help="alpha/beta split path for --profile-case (default: the library's choice)")
+    ap.add_argument("--das-electrons", type=int, default=0, help="electrons per spin of a DAS --profile-case")
     return ap.parse_args()
 
 
@@ -138,6 +143,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _kernel_sources_sha() -> str:
+    """Digest of the CUDA sources of the split contraction kernels (the traffic recorded
+    under profiles/ is reported only while these are unchanged)."""
+    import hashlib
+
+    hsh = hashlib.sha256()
+    for fn in ("ozaki.cu", "ozaki_gemm.cu", "oz_gemm.cuh", "tc_ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2505_20375_gb300", "csrc", fn), "rb") as fh:
+            hsh.update(fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def _traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from profiles/traffic.md (rows
+    "| kernel | workload | sources sha | dram bytes per launch | ..."), or None when no
+    capture of the current sources exists."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    sha = _kernel_sources_sha()
+    for line in open(path):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 4 and cells[0] == kernel and cells[1] == workload and cells[2] == sha:
+            try:
+                return float(cells[3])
+            except ValueError:
+                return None
+    return None
+
+
 def _build_fci(fci, synth, name):
     w = synth.WORKLOADS[name]
     h, g = synth.real_integrals(w["n"], w["n_chol"], w["seed"])
@@ -151,10 +186,14 @@ def _build_das(fci, synth, name, nel):
     return f.build_das(w["spaces"], w["ref"], w["ref"], w["max_transfer"])
 
 
-def _build_spinor(fci, synth):
-    w = synth.WORKLOADS["spinor_24s12e"]
+def _build_spinor_named(fci, synth, name):
+    w = synth.WORKLOADS[name]
     h, g = synth.complex_integrals(w["n"], w["n_chol"], w["seed"])
     return fci.FCI(0).setup_integrals(h, g).build_strings(w["ne"], -1)
+
+
+def _build_spinor(fci, synth):
+    return _build_spinor_named(fci, synth, "spinor_24s12e")
 
 
 # ------------------------------------------------------------------ our arm
@@ -421,15 +460,26 @@ def run_ours(a, rank, world, local_rank):
                 "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 is not in MEASURED_PEAKS.json)"}
     else:
         peaks = _peaks()
-        pad_m, pad_k = 128, (npair + 15) // 16 * 16
-        bf16_flops = 2.0 * pad_m * pad_k * N * (n_sl * (n_sl + 1) // 2)
+        chosen = (tuned or {}).get("chosen", {})
+        two_pass = chosen.get("path") == "two-pass gemm"
+        products = n_sl * (n_sl + 1) // 2
+        if two_pass:  # bulk-copy GEMM: M = 128 pair rows, K = n_pair_pad rounded to 32, 64-det tiles
+            pad_k = -(-((npair + 15) // 16 * 16) // 32) * 32
+            bf16_flops = 2.0 * 128 * pad_k * (-(-N // 64) * 64) * products
+            kname = f"k_oz_gemm<{n_sl},8> (two-pass: cp.async.bulk-fed tcgen05.mma kind::f16, f16 digit slices)"
+            counted = "executed MMA work: 2 x 128 (pair rows, padded) x K_pad(32) x N_pad(64) x s(s+1)/2"
+        else:  # fused producer kernel: M = 128 pair rows, K = n_pair rounded to 16, NT-det tiles
+            pad_k = (npair + 15) // 16 * 16
+            bf16_flops = 2.0 * 128 * pad_k * N * products
+            kname = f"k_oz_contract<{n_sl},{chosen.get('dets_per_tile', 64)}> (fused producer, tcgen05.mma kind::f16)"
+            counted = "executed MMA work: 2 x 128 (pair rows, padded) x K_pad(16) x N x s(s+1)/2"
         achieved = bf16_flops / (ms_launch * 1e-3) / 1e12
         peak = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "kernel": "k_oz_contract (tcgen05.mma kind::f16, fp16 digit slices)",
-                "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        roof = {"bound": "tensor", "kernel": kname, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": _traffic_record(kname.split(" ")[0], a.workload),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; f16 and bf16 share the rate)",
-                "flops_counted": "executed MMA work: 2 x 128 (pair rows, padded) x K_pad x N x s(s+1)/2"}
+                "flops_counted": counted}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -462,6 +512,40 @@ def run_ours(a, rank, world, local_rank):
         "fp64_peak_tflops_measured": fp64_peak,
     }
     return line
+
+
+def run_profile_case(a):
+    """--steps sigma builds of one workload at one precision, nothing else: the command the
+    ncu captures under profiles/ run."""
+    import torch
+
+    from paper_2505_20375_gb300 import fci, synth
+
+    if a.path:
+        os.environ["FCI_OZ_PATH"] = a.path
+    name = a.profile_case
+    w = synth.WORKLOADS[name]
+    if name.startswith("spinor"):
+        f = _build_spinor_named(fci, synth, name)
+    elif name.startswith("das"):
+        f = _build_das(fci, synth, name, a.das_electrons or sum(w["ref"]))
+    else:
+        f = _build_fci(fci, synth, name)
+    c = torch.from_numpy(synth.random_vector(f.n_det, seed=7, complex_=f.is_complex)).cuda()
+    prec = "fp64" if a.precision in ("fp64", "best") else a.precision
+    sl = a.slices if prec != "fp64" else 0
+    o = f.sigma(c, precision=prec, n_slices=sl)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.steps):
+        f.sigma(c, precision=prec, n_slices=sl, out=o)
+    e1.record()
+    e1.synchronize()
+    if prec != "fp64":
+        f.sync_status()
+    print(json.dumps({"profile_case": name, "precision": prec, "n_slices": sl, "n_det": f.n_det,
+                      "ms_per_sigma": e0.elapsed_time(e1) / max(a.steps, 1)}))
 
 
 # ------------------------------------------------------------ reference arm
@@ -506,6 +590,9 @@ def main():
 
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
+    if a.profile_case:
+        run_profile_case(a)
+        return
     line = run_ours(a, rank, world, local_rank)
     if rank == 0:
         print(json.dumps(line))

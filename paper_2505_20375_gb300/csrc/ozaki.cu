@@ -281,11 +281,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
                 int64_t acc[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) acc[c] = 0;
+                uint32_t vs[S][16];  // all levels of the chunk in flight, one wait
+#pragma unroll
+                for (int l = 0; l < S; ++l) tmem_ld16(tlane + (uint32_t)(l * NT + c0), vs[l]);
+                tmem_ld_wait();
+#pragma unroll
+                for (int l = 0; l < S; ++l) tmem_regs_ready(vs[l]);
 #pragma unroll
                 for (int L = S - 1; L <= 2 * S - 2; ++L) {
-                    uint32_t v[16];
-                    tmem_ld16(tlane + (uint32_t)((L - (S - 1)) * NT + c0), v);
-                    tmem_ld_wait();
+                    const uint32_t *v = vs[L - (S - 1)];
                     if (L < L0) {
 #pragma unroll
                         for (int c = 0; c < 16; ++c)
@@ -443,16 +447,17 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
 }
 
 // Two-pass path, first pass: the digit image of D for the bulk-copy GEMM.  Block (N-tile
-// nt, K-chunk kc) holds S planes of 64 determinants x 32 pairs in canonical K-major core
-// matrices; one CTA of 256 threads fills one block, thread t covering determinant t % 64
-// and pairs 8 (t / 64) .. 8 (t / 64) + 7 of the chunk (pair-table rows past n_pair_pad
-// and determinants past the end give zero digits).
-template <int S>
-__global__ void __launch_bounds__(256) k_fci_split(int64_t ndet, int64_t nsa, int64_t nsb, int npair_pad, int n_kc,
-                                                   int64_t n_blocks, const int32_t *__restrict__ pairA,
-                                                   const int32_t *__restrict__ pairB,
-                                                   const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
+// nt, K-chunk kc) holds S planes of 64 determinants x 8 KCC pairs in canonical K-major
+// core matrices; one CTA of 64 KCC threads fills one block, thread t covering determinant
+// t % 64 and pairs 8 (t / 64) .. 8 (t / 64) + 7 of the chunk (pair-table rows past
+// n_pair_pad and determinants past the end give zero digits).
+template <int S, int KCC>
+__global__ void __launch_bounds__(64 * KCC) k_fci_split(int64_t ndet, int64_t nsa, int64_t nsb, int npair_pad, int n_kc,
+                                                        int64_t n_blocks, const int32_t *__restrict__ pairA,
+                                                        const int32_t *__restrict__ pairB,
+                                                        const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
     constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
+    constexpr int B_PLANE = OZG_N * KCC * 16;
     const int row = threadIdx.x & 63, cc = threadIdx.x >> 6;
     const uint32_t nsb32 = (uint32_t)nsb;
     for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(256) k_fci_split(int64_t ndet, int64_t nsa, in
         int32_t ea[8], eb[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int rs = kc * OZG_KC + cc * 8 + e;
+            const int rs = kc * 8 * KCC + cc * 8 + e;
             const bool ok = live && rs < npair_pad;
             ea[e] = ok ? __ldg(pairA + (int64_t)rs * nsa + ka) : -1;
             eb[e] = ok ? __ldg(pairB + (int64_t)rs * nsb + kb) : -1;
@@ -481,7 +486,7 @@ __global__ void __launch_bounds__(256) k_fci_split(int64_t ndet, int64_t nsa, in
             ylo[e] = (uint32_t)y;
             yhi[e] = (uint32_t)(y >> 32);
         }
-        uint8_t *base = Dimg + (size_t)blk * S * OZG_B_PLANE + ((row >> 3) * 4 + cc) * 128 + (row & 7) * 16;
+        uint8_t *base = Dimg + (size_t)blk * S * B_PLANE + ((row >> 3) * KCC + cc) * 128 + (row & 7) * 16;
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             const uint32_t bj = (uint32_t)(j & 3), sel = bj | ((4u + bj) << 8);
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(256) k_fci_split(int64_t ndet, int64_t nsa, in
 #pragma unroll
             for (int e = 0; e < 8; e += 2)
                 w[e / 2] = j < 4 ? digits_f16x2(ylo[e], ylo[e + 1], sel) : digits_f16x2(yhi[e], yhi[e + 1], sel);
-            *(uint4 *)(base + j * OZG_B_PLANE) = make_uint4(w[0], w[1], w[2], w[3]);
+            *(uint4 *)(base + j * B_PLANE) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
 }
@@ -581,10 +586,26 @@ int oz_prepare_G(fci_context *h, int s) {
     return FCI_OK;
 }
 
-// Two-pass path geometry: one M-tile of 128 pair rows, K = n_pair_pad rounded up to 32.
-static void oz_gemm_geom(const fci_context *h, int &n_kc, int64_t &n_nt) {
-    n_kc = (h->npair_pad + OZG_KC - 1) / OZG_KC;
-    n_nt = (h->ndet + OZG_N - 1) / OZG_N;
+// Two-pass path geometry: one M-tile of 128 pair rows.  K-chunks of 16 (kcc = 2) with the G
+// image resident in shared memory when it fits next to a two-stage ring (K = n_pair_pad),
+// else streamed K-chunks of 32 (kcc = 4, K = n_pair_pad rounded up to 32).
+struct OzTwoPass {
+    int kcc, n_kc;
+    bool resa;
+    int64_t n_nt;
+    size_t d_bytes() const { return (size_t)n_nt * n_kc * OZG_N * kcc * 16; }  // per slice
+};
+static OzTwoPass oz_gemm_geom(const fci_context *h, int s) {
+    OzTwoPass g;
+    g.n_nt = (h->ndet + OZG_N - 1) / OZG_N;
+    g.kcc = 2;
+    g.n_kc = h->npair_pad / 16;
+    g.resa = oz_gemm_ring(s, 2, g.n_kc) > 0;
+    if (!g.resa) {
+        g.kcc = 4;
+        g.n_kc = (h->npair_pad + OZG_KC - 1) / OZG_KC;
+    }
+    return g;
 }
 
 // Both paths' buffers fit (the tuner may switch between them): C_int, then either E_int of
@@ -592,39 +613,36 @@ static void oz_gemm_geom(const fci_context *h, int &n_kc, int64_t &n_nt) {
 size_t oz_workspace_bytes(const fci_context *h, int s) {
     const int64_t ntiles = (h->ndet + OZ_TILE - 1) / OZ_TILE;  // E for the widest tile covers the others
     const size_t fused = al256((size_t)ntiles * h->npair * OZ_TILE * 8);
-    int n_kc;
-    int64_t n_nt;
-    oz_gemm_geom(h, n_kc, n_nt);
-    const size_t two = al256((size_t)n_nt * n_kc * std::max(s, 2) * OZG_B_PLANE) + al256((size_t)n_nt * OZG_M * OZG_N * 8);
+    const OzTwoPass g = oz_gemm_geom(h, std::max(s, 2));
+    const size_t two = al256(g.d_bytes() * std::max(s, 2)) + al256((size_t)g.n_nt * OZG_M * OZG_N * 8);
     return al256((size_t)h->ndet * 8) + std::max(fused, two) + 256;
 }
 
 // G digit image in the A-tile layout of the bulk-copy GEMM ([K-chunk][plane][128 x 32]).
 static int oz_prepare_Gt(fci_context *h, int s) {
-    if (h->Gt_slices == s && h->d_Gt) return FCI_OK;
+    if (h->Gt_slices == s && h->d_Gt) return FCI_OK;  // the layout depends on s only
     int rc = oz_prepare_G(h, s);  // checks, and sh_G
     if (rc) return rc;
     const int np = h->npair;
-    int n_kc;
-    int64_t n_nt;
-    oz_gemm_geom(h, n_kc, n_nt);
+    const OzTwoPass tg = oz_gemm_geom(h, s);
+    const int n_kc = tg.n_kc, kw = 8 * tg.kcc;  // K per chunk
     std::vector<double> G((size_t)np * np);
     if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
         return fci_cuda_check(h, cudaGetLastError(), "G download");
     const int shG = h->G_exp;
     uint64_t bias = 0;
     for (int j = 0; j < s; ++j) bias |= (uint64_t)0x80 << (8 * j);
-    const size_t stageA = (size_t)s * OZG_A_PLANE;
+    const size_t a_plane = (size_t)OZG_M * kw * 2, stageA = (size_t)s * a_plane;
     std::vector<uint16_t> img((size_t)n_kc * stageA / 2, 0);
     for (int m = 0; m < OZG_M; ++m)
-        for (int k = 0; k < n_kc * OZG_KC; ++k) {
+        for (int k = 0; k < n_kc * kw; ++k) {
             int64_t gi = 0;
             if (m < np && k < np) gi = llrint(ldexp(G[(size_t)m * np + k], shG));
             const uint64_t y = (uint64_t)gi + bias;
-            const int kc = k / OZG_KC, kk = k % OZG_KC;
-            const size_t off = (size_t)kc * stageA + ((m >> 3) * 4 + (kk >> 3)) * 128 + (m & 7) * 16 + (kk & 7) * 2;
+            const int kc = k / kw, kk = k % kw;
+            const size_t off = (size_t)kc * stageA + ((m >> 3) * tg.kcc + (kk >> 3)) * 128 + (m & 7) * 16 + (kk & 7) * 2;
             for (int j = 0; j < s; ++j)
-                img[(off + (size_t)j * OZG_A_PLANE) / 2] = half_bits_of_small_int((int)((y >> (8 * j)) & 0xFF) - 128);
+                img[(off + (size_t)j * a_plane) / 2] = half_bits_of_small_int((int)((y >> (8 * j)) & 0xFF) - 128);
         }
     fci_dev_free(h->d_Gt);
     h->d_Gt = nullptr;
@@ -735,16 +753,17 @@ static int oz_num_sms(fci_context *h, int *nsm) {
 static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int s, void *ws, cudaStream_t st) {
     int rc = oz_prepare_Gt(h, s);
     if (rc) return rc;
-    if (!oz_gemm_ring(s)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit the GEMM pipeline", s);
-    int n_kc;
-    int64_t n_nt;
-    oz_gemm_geom(h, n_kc, n_nt);
+    const OzTwoPass tg = oz_gemm_geom(h, s);
+    if (!oz_gemm_ring(s, tg.kcc, tg.resa ? tg.n_kc : 0))
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit the GEMM pipeline", s);
+    const int n_kc = tg.n_kc;
+    const int64_t n_nt = tg.n_nt;
     const int64_t N = h->ndet;
     char *p = (char *)ws;
     int64_t *Cint = (int64_t *)p;
     p += al256((size_t)N * 8);
     uint8_t *Dimg = (uint8_t *)p;
-    p += al256((size_t)n_nt * n_kc * s * OZG_B_PLANE);
+    p += al256(tg.d_bytes() * s);
     int64_t *E = (int64_t *)p;
     p += al256((size_t)n_nt * OZG_M * OZG_N * 8);
     // the misc block sits at the end of the larger of the two layouts
@@ -760,13 +779,14 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
         k_to_fixed<<<nb, 256, 0, st>>>(C, N, s, maxbits, Cint, shC);
         const int64_t nblk = n_nt * n_kc;
         const unsigned gb = (unsigned)std::min<int64_t>(nblk, 152 * 16);
-        switch (s) {
-#define OZ_SPLIT(S_)                                                                                           \
-    case S_:                                                                                                   \
-        k_fci_split<S_><<<gb, 256, 0, st>>>(N, h->nsa, h->nsb, h->npair_pad, n_kc, nblk, h->d_pair_a, h->d_pair_b, \
-                                            Cint, Dimg);                                                       \
+        switch (s * 10 + tg.kcc) {
+#define OZ_SPLIT(S_, K_)                                                                                          \
+    case S_ * 10 + K_:                                                                                            \
+        k_fci_split<S_, K_><<<gb, 64 * K_, 0, st>>>(N, h->nsa, h->nsb, h->npair_pad, n_kc, nblk, h->d_pair_a,      \
+                                                   h->d_pair_b, Cint, Dimg);                                      \
         break;
-            OZ_SPLIT(2) OZ_SPLIT(3) OZ_SPLIT(4) OZ_SPLIT(5) OZ_SPLIT(6) OZ_SPLIT(7)
+            OZ_SPLIT(2, 2) OZ_SPLIT(3, 2) OZ_SPLIT(4, 2) OZ_SPLIT(5, 2) OZ_SPLIT(6, 2) OZ_SPLIT(7, 2)
+            OZ_SPLIT(2, 4) OZ_SPLIT(3, 4) OZ_SPLIT(4, 4) OZ_SPLIT(5, 4) OZ_SPLIT(6, 4) OZ_SPLIT(7, 4)
 #undef OZ_SPLIT
             default: return fci_fail(h, FCI_ERR_UNSUPPORTED, "slice count %d", s);
         }
@@ -782,7 +802,7 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
     a.Dimg = Dimg;
     a.E = E;
     a.status = status;
-    if ((rc = oz_gemm_launch(h, s, 8, a, st))) return rc;
+    if ((rc = oz_gemm_launch(h, s, 8, tg.kcc, tg.resa, a, st))) return rc;
     phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
     const int threads = 128;
     dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
@@ -895,7 +915,8 @@ int oz_tune_candidates(const fci_context *h, int s, int *nt, int *path, int max)
             nt[n] = t;
             path[n++] = 0;
         }
-    if (n < max && s <= 7 && oz_gemm_ring(s)) {  // two-pass: 64-determinant tiles
+    const OzTwoPass tg = oz_gemm_geom(h, s);
+    if (n < max && s <= 7 && oz_gemm_ring(s, tg.kcc, tg.resa ? tg.n_kc : 0)) {  // two-pass: 64-determinant tiles
         nt[n] = 64;
         path[n++] = 1;
     }

@@ -214,7 +214,7 @@ int cz_check(fci_context *h, int s) {
     if ((int64_t)s * nnz * 4096 >= ((int64_t)1 << 24))
         return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices x %lld nonzero terms could exceed 2^24 in a level sum", s,
                         (long long)nnz);
-    if (!oz_gemm_ring(s)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit two pipeline stages", s);
+    if (!oz_gemm_ring(s, 4, 0)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit two pipeline stages", s);
     return FCI_OK;
 }
 
@@ -315,7 +315,7 @@ int cz_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, si
         a.Dimg = Dimg;
         a.E = E;
         a.status = status;
-        if ((rc = oz_gemm_launch(h, s, 7, a, st))) return rc;
+        if ((rc = oz_gemm_launch(h, s, 7, 4, false, a, st))) return rc;
     }
     {
         phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);

@@ -343,14 +343,16 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
                 int64_t acc[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) acc[c] = 0;
+                uint32_t vs[S][16];  // all levels of the chunk in flight, one wait
+#pragma unroll
+                for (int l = 0; l < S; ++l) tmem_ld16(tl + (uint32_t)(l * Np + 16 * ck), vs[l]);
+                tmem_ld_wait();
 #pragma unroll
                 for (int l = 0; l < S; ++l) {
-                    uint32_t v[16];
-                    tmem_ld16(tl + (uint32_t)(l * Np + 16 * ck), v);
-                    tmem_ld_wait();
+                    tmem_regs_ready(vs[l]);
 #pragma unroll
                     for (int c = 0; c < 16; ++c)
-                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (8 * l));
+                        acc[c] += (int64_t)__float2int_rn(__uint_as_float(vs[l][c])) * ((int64_t)1 << (8 * l));
                 }
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {

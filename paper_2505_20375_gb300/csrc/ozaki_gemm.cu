@@ -48,7 +48,7 @@ struct OzgParams {
 struct OzgShared {
     uint64_t full[OZG_MAX_STAGES], empty[OZG_MAX_STAGES];
     uint64_t acc_full[2], acc_empty[2];
-    uint64_t drain;
+    uint64_t drain, a_full;
     uint32_t tmem_base;
     int abort;
 };
@@ -77,16 +77,21 @@ __device__ __forceinline__ bool ozg_wait_warp(uint32_t bar, uint32_t parity, vol
     return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
 }
 
-template <int S, int W>
+// S slices, W-bit digits, KCC core matrices (8 K each) per pipeline stage, RESA: the whole
+// A image (one M-tile) is loaded into shared memory once and only B tiles stream.
+template <int S, int W, int KCC, bool RESA>
 __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constant__ OzgParams p) {
     constexpr int NBUF = (2 * S * OZG_N <= 512) ? 2 : 1;
     constexpr int L0 = oz_gemm_L0(S, W);
-    constexpr uint32_t STAGE_A = S * OZG_A_PLANE, STAGE_B = S * OZG_B_PLANE;
+    constexpr uint32_t A_PLANE = OZG_M * KCC * 16, B_PLANE = OZG_N * KCC * 16;
+    constexpr uint32_t STAGE_A = S * A_PLANE, STAGE_B = S * B_PLANE;
+    constexpr uint32_t STAGE_LOAD = RESA ? STAGE_B : STAGE_A + STAGE_B;
     extern __shared__ __align__(1024) uint8_t cz_smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)cz_smem_raw + 1023) & ~(uintptr_t)1023);
     const int R = p.ring;
-    uint8_t *sA = smem;                              // R stages of S A-planes
-    uint8_t *sB = sA + (size_t)R * STAGE_A;          // R stages of S B-planes
+    // RESA: A region = n_kc x STAGE_A (every K-chunk of the single M-tile); else R stages
+    uint8_t *sA = smem;
+    uint8_t *sB = sA + (RESA ? (size_t)p.n_kc * STAGE_A : (size_t)R * STAGE_A);  // R stages of S B-planes
     OzgShared *sh = (OzgShared *)(sB + (size_t)R * STAGE_B);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -99,6 +104,7 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
             mbar_init(smem_u32(&sh->acc_empty[b]), OZG_EPI_WARPS);
         }
         mbar_init(smem_u32(&sh->drain), 1);
+        mbar_init(smem_u32(&sh->a_full), 1);
         sh->abort = 0;
         fence_barrier_init();
     }
@@ -116,6 +122,12 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------------------ bulk copies
+            if (RESA) {  // the whole A image, in pieces of at most 32 KB, on its own barrier
+                const uint32_t total = (uint32_t)p.n_kc * STAGE_A, ab = smem_u32(&sh->a_full);
+                mbar_expect_tx(ab, total);
+                for (uint32_t o = 0; o < total; o += 32768u)
+                    bulk_g2s(smem_u32(sA + o), p.Gimg + o, total - o < 32768u ? total - o : 32768u, ab);
+            }
             uint32_t q = 0;
             for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
                 const int64_t nt = u / p.n_mt;
@@ -132,8 +144,8 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
                         break;
                     }
                     const uint32_t fb = smem_u32(&sh->full[st]);
-                    mbar_expect_tx(fb, STAGE_A + STAGE_B);
-                    bulk_g2s(smem_u32(sA + (size_t)st * STAGE_A), ga + (size_t)kc * STAGE_A, STAGE_A, fb);
+                    mbar_expect_tx(fb, STAGE_LOAD);
+                    if (!RESA) bulk_g2s(smem_u32(sA + (size_t)st * STAGE_A), ga + (size_t)kc * STAGE_A, STAGE_A, fb);
                     bulk_g2s(smem_u32(sB + (size_t)st * STAGE_B), gb + (size_t)kc * STAGE_B, STAGE_B, fb);
                 }
                 if (!ok) break;
@@ -143,10 +155,11 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
         if (lane == 0) {
             // ------------------------------------------------------------ MMA issuer
             const uint32_t idesc = idesc_f16(OZG_M, OZG_N);
-            const uint64_t a0 = smem_desc(smem_u32(sA), 128, 4 * 128);
-            const uint64_t b0 = smem_desc(smem_u32(sB), 128, 4 * 128);
+            const uint64_t a0 = smem_desc(smem_u32(sA), 128, KCC * 128);
+            const uint64_t b0 = smem_desc(smem_u32(sB), 128, KCC * 128);
             uint32_t q = 0, tau = 0;
             bool issued = false, ok = true;
+            if (RESA && !ozg_wait(smem_u32(&sh->a_full), 0, abort, p.status, p.timeout_cycles)) ok = false;
             for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++tau) {
                 const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
                 if (tau >= (uint32_t)NBUF) {
@@ -162,18 +175,18 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t as = a0 + (uint64_t)((st * STAGE_A) >> 4);
+                    const uint64_t as = a0 + (uint64_t)(((RESA ? kc : st) * STAGE_A) >> 4);
                     const uint64_t bs = b0 + (uint64_t)((st * STAGE_B) >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < OZG_KC / 16; ++kk) {
+                    for (int kk = 0; kk < KCC / 2; ++kk) {
 #pragma unroll
                         for (int j = S - 1; j >= 0; --j) {
-                            const uint64_t b = bs + (uint64_t)((j * OZG_B_PLANE + kk * 256) >> 4);
+                            const uint64_t b = bs + (uint64_t)((j * B_PLANE + kk * 256) >> 4);
                             const uint32_t acc_in = (kc != 0 || kk != 0 || j != S - 1) ? 1u : 0u;
 #pragma unroll
                             for (int i = S - 1 - j; i < S; ++i)
                                 mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * OZG_N),
-                                        as + (uint64_t)((i * OZG_A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
+                                        as + (uint64_t)((i * A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
                         }
                     }
                     issued = true;
@@ -214,11 +227,15 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
                 int64_t acc[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) acc[c] = 0;
+                uint32_t vs[S][16];  // all levels of the chunk in flight, one wait
+#pragma unroll
+                for (int l = 0; l < S; ++l) tmem_ld16(tl + (uint32_t)(l * OZG_N + c0), vs[l]);
+                tmem_ld_wait();
+#pragma unroll
+                for (int l = 0; l < S; ++l) tmem_regs_ready(vs[l]);
 #pragma unroll
                 for (int L = S - 1; L <= 2 * S - 2; ++L) {
-                    uint32_t v[16];
-                    tmem_ld16(tl + (uint32_t)((L - (S - 1)) * OZG_N + c0), v);
-                    tmem_ld_wait();
+                    const uint32_t *v = vs[L - (S - 1)];
                     if (L < L0) {
 #pragma unroll
                         for (int c = 0; c < 16; ++c)
@@ -234,7 +251,6 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
                             acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - L0)));
                     }
                 }
-#pragma unroll
                 if (mt * OZG_M + row < p.M_real)  // rows past the operator's size are never read
 #pragma unroll
                     for (int c = 0; c < 16; c += 2)
@@ -252,16 +268,16 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
 }
 
 
-template <int W>
+template <int W, int KCC, bool RESA>
 void (*oz_gemm_kernel(int s))(const OzgParams) {
     switch (s) {
-        case 2: return k_oz_gemm<2, W>;
-        case 3: return k_oz_gemm<3, W>;
-        case 4: return k_oz_gemm<4, W>;
-        case 5: return k_oz_gemm<5, W>;
-        case 6: return k_oz_gemm<6, W>;
-        case 7: return k_oz_gemm<7, W>;
-        case 8: return k_oz_gemm<8, W>;
+        case 2: return k_oz_gemm<2, W, KCC, RESA>;
+        case 3: return k_oz_gemm<3, W, KCC, RESA>;
+        case 4: return k_oz_gemm<4, W, KCC, RESA>;
+        case 5: return k_oz_gemm<5, W, KCC, RESA>;
+        case 6: return k_oz_gemm<6, W, KCC, RESA>;
+        case 7: return k_oz_gemm<7, W, KCC, RESA>;
+        case 8: return k_oz_gemm<8, W, KCC, RESA>;
         default: return nullptr;
     }
 }
@@ -270,16 +286,24 @@ size_t oz_gemm_fixed() { return 1024 + sizeof(OzgShared) + 64; }
 
 }  // namespace
 
-int oz_gemm_ring(int s) {
-    const size_t stage = (size_t)s * (OZG_A_PLANE + OZG_B_PLANE);
-    const size_t r = (OZG_SMEM_MAX - oz_gemm_fixed()) / stage;
+int oz_gemm_ring(int s, int kcc, int resa_kc) {
+    const size_t a_plane = (size_t)OZG_M * kcc * 16, b_plane = (size_t)OZG_N * kcc * 16;
+    const size_t resident = resa_kc > 0 ? (size_t)resa_kc * s * a_plane : 0;
+    const size_t stage = (size_t)s * ((resa_kc > 0 ? 0 : a_plane) + b_plane);
+    const size_t fixed = oz_gemm_fixed() + resident;
+    if (fixed >= OZG_SMEM_MAX) return 0;
+    const size_t r = (OZG_SMEM_MAX - fixed) / stage;
     return r < 2 ? 0 : (int)std::min<size_t>(OZG_MAX_STAGES, r);
 }
 
-int oz_gemm_launch(fci_context *h, int s, int w, const oz_gemm_args &a, cudaStream_t st) {
-    void (*kern)(const OzgParams) = w == 7 ? oz_gemm_kernel<7>(s) : w == 8 ? oz_gemm_kernel<8>(s) : nullptr;
-    const int ring = oz_gemm_ring(s);
-    if (!kern || !ring) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split GEMM: %d slices of %d bits", s, w);
+int oz_gemm_launch(fci_context *h, int s, int w, int kcc, bool resa, const oz_gemm_args &a, cudaStream_t st) {
+    void (*kern)(const OzgParams) = nullptr;
+    if (w == 7 && kcc == 4 && !resa) kern = oz_gemm_kernel<7, 4, false>(s);
+    if (w == 8 && kcc == 2 && resa) kern = oz_gemm_kernel<8, 2, true>(s);
+    if (w == 8 && kcc == 4 && !resa) kern = oz_gemm_kernel<8, 4, false>(s);
+    if (resa && a.n_mt != 1) kern = nullptr;
+    const int ring = oz_gemm_ring(s, kcc, resa ? a.n_kc : 0);
+    if (!kern || !ring) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split GEMM: %d slices of %d bits (K-chunk %d, resident %d)", s, w, 8 * kcc, (int)resa);
     OzgParams prm;
     prm.n_mt = a.n_mt;
     prm.n_kc = a.n_kc;
@@ -295,7 +319,9 @@ int oz_gemm_launch(fci_context *h, int s, int w, const oz_gemm_args &a, cudaStre
     prm.timeout_cycles = (long long)((to ? atof(to) : 2000.0) * 2.1e6);
     int nsm = 0;
     FCI_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
-    const size_t smem = oz_gemm_fixed() + (size_t)ring * s * (OZG_A_PLANE + OZG_B_PLANE);
+    const size_t a_plane = (size_t)OZG_M * kcc * 16, b_plane = (size_t)OZG_N * kcc * 16;
+    const size_t smem = oz_gemm_fixed() + (resa ? (size_t)a.n_kc * s * a_plane : 0) +
+                        (size_t)ring * s * ((resa ? 0 : a_plane) + b_plane);
     FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t units = a.n_nt * a.n_mt;
     phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);

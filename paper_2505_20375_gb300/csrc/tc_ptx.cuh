@@ -83,6 +83,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// Orders every use of r after the preceding tcgen05.wait::ld (the registers of an
+// asynchronous TMEM load are valid only after the wait): an empty volatile statement that
+// reads and writes r, placed after the wait.
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[16]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor, no swizzle (canonical K-major core matrices of
 // 8 rows x 16 bytes): lbo = byte stride between core matrices along K, sbo = byte
 // stride between 8-row groups along M/N.  Version field 1 (bits 46-47).

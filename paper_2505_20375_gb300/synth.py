@@ -155,4 +155,6 @@ WORKLOADS = {
     "das_16o_4x4": dict(n=16, spaces=[4, 4, 4, 4], ref=[2, 2, 2, 2], max_transfer=2, n_chol=48, seed=3),
     "das_16o_4x4_8e": dict(n=16, spaces=[4, 4, 4, 4], ref=[1, 1, 1, 1], max_transfer=1, n_chol=48, seed=5),
     "spinor_24s12e": dict(n=24, ne=12, n_chol=48, seed=4),
+    # a smaller spinor problem of the same shape family (profiling captures)
+    "spinor_20s10e": dict(n=20, ne=10, n_chol=40, seed=4),
 }
