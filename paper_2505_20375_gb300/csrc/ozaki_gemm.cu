@@ -1,9 +1,12 @@
-// Kernel layout (one persistent CTA per SM, 320 threads):
+// Kernel layout (one persistent CTA per SM, 320 or 576 threads):
 //   warp 0     lane 0 issues the two bulk copies of each pipeline stage (A tile: s planes
 //              of 128 x 32, B tile: s planes of 64 x 32), completing on the stage's mbarrier;
 //   warp 1     allocates TMEM; lane 0 issues the MMAs (M = 128, N = 64, K = 16) into the
 //              s level accumulators and commits;
-//   warps 2-9  epilogue, two per TMEM lane quadrant (32 columns each).
+//   warps 2..  epilogue: 8 warps (two per TMEM lane quadrant, 32 columns each) when the
+//              accumulators are double-buffered (s <= 4), else 16 (four per quadrant,
+//              16 columns each), which for s <= 6 load all levels of their columns
+//              into registers and release the accumulator before combining.
 // Level accumulators are double-buffered when 2 s x 64 TMEM columns fit in 512.  Work units
 // are (N-tile, M-tile) pairs, N-tile outer and dealt round-robin, so the M-tiles of one
 // B tile run at about the same time and its reads hit L2.  Every mbarrier wait is bounded
@@ -20,8 +23,10 @@ namespace {
 
 using namespace tc;
 
-constexpr int OZG_EPI_WARPS = 8;  // two per TMEM lane quadrant, 32 columns each
-constexpr int OZG_THREADS = 32 * (2 + OZG_EPI_WARPS);  // 320
+// Epilogue warps: 8 (two per TMEM lane quadrant, 32 columns each) when the level
+// accumulators are double-buffered, 16 (four per quadrant, 16 columns each) otherwise.
+__host__ __device__ constexpr int ozg_epi_warps(int s) { return 2 * s * OZG_N <= 512 ? 8 : 16; }
+__host__ __device__ constexpr int ozg_threads(int s) { return 32 * (2 + ozg_epi_warps(s)); }
 constexpr int OZG_MAX_STAGES = 6;
 constexpr size_t OZG_SMEM_MAX = 232448 - 1024;
 
@@ -80,7 +85,7 @@ __device__ __forceinline__ bool ozg_wait_warp(uint32_t bar, uint32_t parity, vol
 // S slices, W-bit digits, KCC core matrices (8 K each) per pipeline stage, RESA: the whole
 // A image (one M-tile) is loaded into shared memory once and only B tiles stream.
 template <int S, int W, int KCC, bool RESA>
-__global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constant__ OzgParams p) {
+__global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_constant__ OzgParams p) {
     constexpr int NBUF = (2 * S * OZG_N <= 512) ? 2 : 1;
     constexpr int L0 = oz_gemm_L0(S, W);
     constexpr uint32_t A_PLANE = OZG_M * KCC * 16, B_PLANE = OZG_N * KCC * 16;
@@ -101,7 +106,7 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&sh->acc_full[b]), 1);
-            mbar_init(smem_u32(&sh->acc_empty[b]), OZG_EPI_WARPS);
+            mbar_init(smem_u32(&sh->acc_empty[b]), ozg_epi_warps(S));
         }
         mbar_init(smem_u32(&sh->drain), 1);
         mbar_init(smem_u32(&sh->a_full), 1);
@@ -208,10 +213,17 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
         }
     } else {
         // ---------------------------------------------------------------- epilogue
+        // Warp (quadrant qd, part) owns lanes 32 qd .. 32 qd + 31 and columns
+        // 16 part .. 16 part + 15.  For s <= 6 every level of those columns fits in
+        // registers: the warp loads them all, hands the accumulator back to the MMA warp at
+        // once (so the next unit's MMAs overlap this unit's combination and stores), then
+        // combines.  For larger s it combines level by level and releases at the end.
+        constexpr int CH = OZG_N / (4 * ozg_epi_warps(S));  // 16-column chunks per warp: 2 or 1
         const int qd = warp & 3;
-        const int cbeg = (OZG_N / 2) * ((warp - 2) >> 2);  // this warp's half of the columns
+        const int cw = 16 * CH * ((warp - 2) >> 2);
         const int row = 32 * qd + lane;
         constexpr int lowshift = W * (L0 - (S - 1));
+        constexpr bool EARLY = NBUF == 1 && S <= 6;
         uint32_t tau = 0;
         for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++tau) {
             const int64_t nt = u / p.n_mt;
@@ -220,45 +232,84 @@ __global__ void __launch_bounds__(OZG_THREADS, 1) k_oz_gemm(const __grid_constan
             const uint32_t par = NBUF == 2 ? (tau >> 1) & 1 : tau & 1;
             if (!ozg_wait_warp(smem_u32(&sh->acc_full[buf]), par, abort, p.status, p.timeout_cycles)) break;
             tc_fence_after();
-            const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * OZG_N);
-            int64_t *dst_row = p.E + ((size_t)nt * p.M_pad + (size_t)mt * OZG_M + row) * OZG_N;
-#pragma unroll 1
-            for (int c0 = cbeg; c0 < cbeg + OZG_N / 2; c0 += 16) {
-                int64_t acc[16];
+            const uint32_t tl0 = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * OZG_N + cw);
+            int64_t *dst0 = p.E + ((size_t)nt * p.M_pad + (size_t)mt * OZG_M + row) * OZG_N + cw;
+            const bool keep = mt * OZG_M + row < p.M_real;  // rows past the operator's size are never read
+            if (EARLY) {  // CH == 1
+                const uint32_t tl = tl0;
+                int64_t *dst = dst0;
+                uint32_t vs[S][16];
 #pragma unroll
-                for (int c = 0; c < 16; ++c) acc[c] = 0;
-                uint32_t vs[S][16];  // all levels of the chunk in flight, one wait
-#pragma unroll
-                for (int l = 0; l < S; ++l) tmem_ld16(tl + (uint32_t)(l * OZG_N + c0), vs[l]);
+                for (int l = 0; l < S; ++l) tmem_ld16(tl + (uint32_t)(l * OZG_N), vs[l]);
                 tmem_ld_wait();
 #pragma unroll
                 for (int l = 0; l < S; ++l) tmem_regs_ready(vs[l]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
 #pragma unroll
-                for (int L = S - 1; L <= 2 * S - 2; ++L) {
-                    const uint32_t *v = vs[L - (S - 1)];
-                    if (L < L0) {
+                for (int c = 0; c < 16; c += 2) {
+                    int64_t a[2] = {0, 0};
 #pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - (S - 1))));
-                    } else {
-                        if (L == L0 && lowshift > 0) {
+                    for (int h = 0; h < 2; ++h)
+#pragma unroll
+                        for (int L = S - 1; L <= 2 * S - 2; ++L) {
+                            const int64_t v = (int64_t)__float2int_rn(__uint_as_float(vs[L - (S - 1)][c + h]));
+                            if (L < L0) {
+                                a[h] += v * ((int64_t)1 << (W * (L - (S - 1))));
+                            } else {
+                                if (L == L0 && lowshift > 0)
+                                    a[h] = (a[h] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
+                                a[h] += v * ((int64_t)1 << (W * (L - L0)));
+                            }
+                        }
+                    if (keep) __stcs((longlong2 *)(dst + c), make_longlong2(a[0], a[1]));
+                }
+            } else {
+                // combine level by level; with one chunk per warp (single-buffered
+                // accumulators) release before the stores, with two (double-buffered) after
+#pragma unroll 1
+                for (int ch = 0; ch < CH; ++ch) {
+                    int64_t acc[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) acc[c] = 0;
+#pragma unroll
+                    for (int L = S - 1; L <= 2 * S - 2; ++L) {
+                        uint32_t v[16];
+                        tmem_ld16(tl0 + (uint32_t)((L - (S - 1)) * OZG_N + 16 * ch), v);
+                        tmem_ld_wait();
+                        tmem_regs_ready(v);
+                        if (L < L0) {
 #pragma unroll
                             for (int c = 0; c < 16; ++c)
-                                acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
+                                acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - (S - 1))));
+                        } else {
+                            if (L == L0 && lowshift > 0) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c)
+                                    acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
+                            }
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - L0)));
                         }
-#pragma unroll
-                        for (int c = 0; c < 16; ++c)
-                            acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - L0)));
                     }
-                }
-                if (mt * OZG_M + row < p.M_real)  // rows past the operator's size are never read
+                    if (CH == 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
+                    }
+                    if (keep)
 #pragma unroll
-                    for (int c = 0; c < 16; c += 2)
-                        __stcs((longlong2 *)(dst_row + c0 + c), make_longlong2(acc[c], acc[c + 1]));
+                        for (int c = 0; c < 16; c += 2)
+                            __stcs((longlong2 *)(dst0 + 16 * ch + c), make_longlong2(acc[c], acc[c + 1]));
+                }
+                if (CH != 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
+                }
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
         }
     }
     tc_fence_before();
@@ -325,7 +376,7 @@ int oz_gemm_launch(fci_context *h, int s, int w, int kcc, bool resa, const oz_ge
     FCI_CUDA(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t units = a.n_nt * a.n_mt;
     phase_scope ps(h, st, FCI_PHASE_CONTRACT, 1);
-    kern<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm, units)), OZG_THREADS, smem, st>>>(prm);
+    kern<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(nsm, units)), ozg_threads(s), smem, st>>>(prm);
     FCI_CUDA(h, cudaGetLastError());
     return FCI_OK;
 }
