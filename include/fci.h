@@ -178,6 +178,10 @@ typedef struct {
                                FCI_PREC_OZ_BF16 with final_slices >= 6 (error below
                                1e-11 of ||sigma||, the FP64 parity bar) */
     int final_slices;
+    int staged_sigma;       /* step-wise ABI: 1 = every sigma request uses the same two
+                               vectors of the workspace (x copied in, y copied out by the
+                               library), so a caller can replay a captured sigma graph for
+                               the whole solve; default 0 */
 } fci_davidson_opts;
 
 typedef struct {
@@ -273,6 +277,18 @@ typedef struct {
  * appear in at most one job.  Asynchronous.  This is the batching the serving loop uses
  * for the sigma builds of concurrent Davidson solves (not a step of the paper's method). */
 int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream);
+
+/* fci_sigma_grouped replayed from a CUDA graph: the first call with a given job list (every
+ * field of every job equal, same stream) runs it once, then captures its launches into a
+ * graph kept in a process-wide cache (at most 16 lists; the oldest is dropped); later
+ * calls with the same list launch the graph.  Destroying a handle, or rebuilding its
+ * strings or integrals, drops the graphs that name it.  `stream` must not be the legacy
+ * default stream (the list is then run without a graph) nor itself be capturing.  Results
+ * equal fci_sigma_grouped's.  This is how the serving loop replays the batched sigma
+ * builds of its active solves while the set of solves does not change. */
+int fci_sigma_grouped_graph(const fci_sigma_job *jobs, int n_jobs, fci_stream stream);
+/* Drop every cached grouped graph. */
+int fci_clear_grouped_graphs(void);
 
 typedef struct fci_davidson_state *fci_davidson_handle;
 

@@ -399,6 +399,7 @@ struct fci_davidson_state {
     double E_prev = 0.0, lam_pending = 0.0;
     int request = REQ_NONE;
     double *req_x = nullptr, *req_y = nullptr;
+    double *stage_x = nullptr, *stage_y = nullptr, *real_y = nullptr;  // staged sigma requests
     std::chrono::steady_clock::time_point t_iter;
     std::vector<fci_davidson_iter> log;
     int status = FCI_OK;
@@ -430,11 +431,18 @@ struct fci_davidson_state {
         FCI_CUDA(h, cudaGetLastError());
         return FCI_OK;
     }
-    void ask(int kind, double *x, double *yv) {
+    int ask(int kind, double *x, double *yv) {
         request = kind;
         req_x = x;
         req_y = yv;
         ++n_sigma;
+        if (o.staged_sigma) {  // the caller always sees the same two vectors
+            FCI_CUDA(h, cudaMemcpyAsync(stage_x, x, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            req_x = stage_x;
+            req_y = stage_y;
+            real_y = yv;
+        }
+        return FCI_OK;
     }
 
     int init(fci_context *hh, const fci_davidson_opts *oo, const void *guess, void *ws, cudaStream_t st) {
@@ -456,6 +464,10 @@ struct fci_davidson_state {
         scp = (double *)p; p += vec;
         t = (double *)p; p += vec;
         diag = (double *)p; p += al((size_t)n * 8);
+        if (o.staged_sigma) {
+            stage_x = (double *)p; p += vec;
+            stage_y = (double *)p; p += vec;
+        }
         sig_ws = p;
         size_t sig = sigma_ws_bytes(h, o.precision, o.n_slices);
         if (o.precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, o.final_precision, o.final_slices));
@@ -485,13 +497,14 @@ struct fci_davidson_state {
             k_set_unit<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, cplx, argmin);
         }
         FCI_CUDA(h, normalize(Vk(0), nrm));
-        ask(REQ_INIT, Vk(0), Sk(0));
-        return FCI_OK;
+        return ask(REQ_INIT, Vk(0), Sk(0));
     }
 
     // The caller has written y = H x for the pending request.
     int consume_sigma() {
         int rc;
+        if (o.staged_sigma && request != REQ_NONE)
+            FCI_CUDA(h, cudaMemcpyAsync(real_y, stage_y, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
         switch (request) {
             case REQ_INIT:
                 FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
@@ -568,8 +581,7 @@ struct fci_davidson_state {
                     FCI_CUDA(h, cudaMemcpyAsync(Vk(0), c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
                     FCI_CUDA(h, normalize(Vk(0), nrm));
                     lam_pending = lam;
-                    ask(REQ_SWITCH, Vk(0), Sk(0));
-                    return FCI_OK;
+                    return ask(REQ_SWITCH, Vk(0), Sk(0));
                 }
             } else if (rn <= o.tol_residual && it > 1 && fabs(dE) <= o.tol_energy) {
                 converged = true;
@@ -641,8 +653,7 @@ struct fci_davidson_state {
             }
             k_scale<<<vb, RED_THREADS, 0, s>>>(t, nreal, nrm);
             FCI_CUDA(h, cudaMemcpyAsync(Vk(k), t, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-            ask(REQ_APPEND, Vk(k), Sk(k));
-            return FCI_OK;
+            return ask(REQ_APPEND, Vk(k), Sk(k));
         }
         return FCI_OK;
     }
@@ -671,7 +682,7 @@ size_t davidson_ws_bytes(const fci_context *h, const fci_davidson_opts *o) {
     const size_t vec = al((size_t)n * esz);
     size_t sig = sigma_ws_bytes(h, o->precision, o->n_slices);
     if (o->precision != FCI_PREC_FP64) sig = std::max(sig, sigma_ws_bytes(h, o->final_precision, o->final_slices));
-    return 2 * (size_t)o->max_subspace * vec + 5 * vec + al((size_t)n * 8) + al(sig);
+    return 2 * (size_t)o->max_subspace * vec + (o->staged_sigma ? 7 : 5) * vec + al((size_t)n * 8) + al(sig);
 }
 
 int davidson_run(fci_context *h, const fci_davidson_opts *o, double *C_io, double *energy, fci_davidson_log *log,

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <complex>
+#include <mutex>
 
 #include "fci_internal.h"
 
@@ -100,9 +101,47 @@ static int set_dev(fci_context *h) {
     return FCI_OK;
 }
 
+// Process-wide cache of grouped sigma graphs, keyed by the whole job list and the stream.
+namespace {
+struct grouped_graph_rec {
+    std::vector<fci_sigma_job> jobs;
+    cudaStream_t stream;
+    int device;
+    cudaGraphExec_t exec;
+};
+std::vector<grouped_graph_rec> g_grouped_graphs;
+std::mutex g_grouped_mu;
+
+bool same_jobs(const std::vector<fci_sigma_job> &a, const fci_sigma_job *b, int n) {
+    if ((int)a.size() != n) return false;
+    for (int i = 0; i < n; ++i)
+        if (a[i].handle != b[i].handle || a[i].C != b[i].C || a[i].sigma != b[i].sigma ||
+            a[i].precision != b[i].precision || a[i].n_slices != b[i].n_slices || a[i].workspace != b[i].workspace ||
+            a[i].workspace_bytes != b[i].workspace_bytes)
+            return false;
+    return true;
+}
+}  // namespace
+
+// Drops the grouped graphs that name h (its buffers or tables are about to change).
+static void drop_grouped_graphs_of(const fci_context *h) {
+    std::lock_guard<std::mutex> lk(g_grouped_mu);
+    for (size_t i = 0; i < g_grouped_graphs.size();) {
+        bool uses = false;
+        for (const auto &j : g_grouped_graphs[i].jobs) uses |= j.handle == h;
+        if (uses) {
+            cudaGraphExecDestroy(g_grouped_graphs[i].exec);
+            g_grouped_graphs.erase(g_grouped_graphs.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
 static void drop_graphs(fci_context *h) {
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    drop_grouped_graphs_of(h);
 }
 
 static void free_strings(fci_context *h) {
@@ -500,6 +539,7 @@ void fci_davidson_default_opts(fci_davidson_opts *o) {
     o->use_guess = 0;
     o->final_precision = FCI_PREC_FP64;
     o->final_slices = 0;
+    o->staged_sigma = 0;
 }
 
 static int check_opts(fci_context *h, const fci_davidson_opts *o) {
@@ -744,6 +784,61 @@ int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream) 
         int rc = sigma_dispatch(j.handle, j.C, j.sigma, j.precision, j.n_slices, j.workspace, j.workspace_bytes, s);
         if (rc) return rc;
     }
+    return FCI_OK;
+}
+
+int fci_clear_grouped_graphs(void) {
+    std::lock_guard<std::mutex> lk(g_grouped_mu);
+    for (auto &g : g_grouped_graphs) cudaGraphExecDestroy(g.exec);
+    g_grouped_graphs.clear();
+    return FCI_OK;
+}
+
+int fci_sigma_grouped_graph(const fci_sigma_job *jobs, int n_jobs, fci_stream stream) {
+    if (!jobs || n_jobs <= 0) return fci_sigma_grouped(jobs, n_jobs, stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    fci_context *h0 = jobs[0].handle;
+    if (!h0) return fci_fail(nullptr, FCI_ERR_ARG, "job 0 has no handle");
+    {
+        std::lock_guard<std::mutex> lk(g_grouped_mu);
+        for (auto &g : g_grouped_graphs)
+            if (g.stream == s && g.device == h0->device && same_jobs(g.jobs, jobs, n_jobs)) {
+                FCI_CUDA(h0, cudaSetDevice(h0->device));
+                FCI_CUDA(h0, cudaGraphLaunch(g.exec, s));
+                return FCI_OK;
+            }
+    }
+    // first call with this list: a plain run (validates, prepares digit images and kernel
+    // attributes), then the capture
+    int rc = fci_sigma_grouped(jobs, n_jobs, stream);
+    if (rc || s == nullptr) return rc;
+    std::vector<char> timing(n_jobs);
+    for (int i = 0; i < n_jobs; ++i) {
+        timing[i] = jobs[i].handle->timing;
+        jobs[i].handle->timing = false;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = fci_sigma_grouped(jobs, n_jobs, stream);
+        e = cudaStreamEndCapture(s, &graph);
+    }
+    for (int i = 0; i < n_jobs; ++i) jobs[i].handle->timing = timing[i];
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return fci_cuda_check(h0, e, "grouped sigma capture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fci_cuda_check(h0, e, "cudaGraphInstantiate");
+    std::lock_guard<std::mutex> lk(g_grouped_mu);
+    if (g_grouped_graphs.size() >= 16) {
+        cudaGraphExecDestroy(g_grouped_graphs.front().exec);
+        g_grouped_graphs.erase(g_grouped_graphs.begin());
+    }
+    g_grouped_graphs.push_back({std::vector<fci_sigma_job>(jobs, jobs + n_jobs), s, h0->device, exec});
     return FCI_OK;
 }
 

@@ -516,11 +516,13 @@ int oz_ring(int s, int KC, int nt) {
 // environment (32 or 64), else 64.
 // Contraction path for s slices: 1 = two-pass (digit image of D in HBM, then the
 // bulk-copy GEMM), 0 = fused producer kernel.  The tuner's choice, else FCI_OZ_PATH
-// ("gemm" / "fused") from the environment, else fused.
+// ("gemm" / "fused") from the environment, else two-pass from 2^20 determinants on (where
+// it was measured faster at every slice count) and fused below (small problems, which
+// also share grouped launches).
 int oz_path(const fci_context *h, int s) {
     if (s >= 2 && s <= 8 && h->oz_tuned_nt[s]) return h->oz_tuned_path[s];
     if (const char *env = getenv("FCI_OZ_PATH")) return strcmp(env, "gemm") == 0 ? 1 : 0;
-    return 0;
+    return (h->ndet >= ((int64_t)1 << 20) && s <= 7) ? 1 : 0;
 }
 int oz_nt(const fci_context *h, int s) {
     if (s >= 2 && s <= 8 && h->oz_tuned_nt[s]) return h->oz_tuned_nt[s];

@@ -46,7 +46,7 @@ class fci_info(ctypes.Structure):
 class fci_davidson_opts(ctypes.Structure):
     _fields_ = [("max_iter", _i32), ("max_subspace", _i32), ("tol_residual", _dbl), ("tol_energy", _dbl),
                 ("eps", _dbl), ("precision", _i32), ("n_slices", _i32), ("switch_residual", _dbl),
-                ("use_guess", _i32), ("final_precision", _i32), ("final_slices", _i32)]
+                ("use_guess", _i32), ("final_precision", _i32), ("final_slices", _i32), ("staged_sigma", _i32)]
 
 
 class fci_davidson_iter(ctypes.Structure):
@@ -104,6 +104,8 @@ class fci_sigma_job(ctypes.Structure):
 
 
 _sigma_grouped = _sig("fci_sigma_grouped", [ctypes.POINTER(fci_sigma_job), _i32, _vp])
+_sigma_grouped_graph = _sig("fci_sigma_grouped_graph", [ctypes.POINTER(fci_sigma_job), _i32, _vp])
+_clear_grouped_graphs = _sig("fci_clear_grouped_graphs", [])
 _dav_begin = _sig("davidson_begin", [_vp, ctypes.POINTER(fci_davidson_opts), _vp, _vp, _sz, _vp, ctypes.POINTER(_vp)])
 _dav_request = _sig("davidson_request", [_vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_i32),
                                          ctypes.POINTER(_i32), ctypes.POINTER(_vp), ctypes.POINTER(_sz)])
@@ -290,7 +292,7 @@ class FCI:
 
     def davidson_opts(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                       precision="fp64", n_slices=6, switch_residual=1e-5, final_precision="fp64", final_slices=0,
-                      use_guess=False) -> fci_davidson_opts:
+                      use_guess=False, staged_sigma=False) -> fci_davidson_opts:
         o = fci_davidson_opts()
         _dav_defaults(ctypes.byref(o))
         o.max_iter, o.max_subspace = max_iter, max_subspace
@@ -298,6 +300,7 @@ class FCI:
         o.precision, o.n_slices, o.switch_residual = PRECISIONS[precision], n_slices, switch_residual
         o.final_precision, o.final_slices = PRECISIONS[final_precision], final_slices
         o.use_guess = 1 if use_guess else 0
+        o.staged_sigma = 1 if staged_sigma else 0
         return o
 
     def davidson_workspace_bytes(self, opts: fci_davidson_opts) -> int:
@@ -361,17 +364,28 @@ class FCI:
 
 # ---------------------------------------------------------------- batched steps
 
-def sigma_grouped(jobs, stream=None):
-    """jobs: list of (FCI, C, sigma, precision, n_slices, workspace_ptr, workspace_bytes);
-    one fci_sigma_grouped call (split-precision jobs share one contraction launch)."""
+def _job_array(jobs):
     arr = (fci_sigma_job * len(jobs))()
     for i, (f, C, out, prec, sl, ws, wsb) in enumerate(jobs):
         arr[i] = fci_sigma_job(f._h, _vp(C if isinstance(C, int) else C.data_ptr()),
                                _vp(out if isinstance(out, int) else out.data_ptr()),
                                PRECISIONS[prec] if isinstance(prec, str) else prec, sl, _vp(ws), wsb)
-    rc = _sigma_grouped(arr, len(jobs), _stream(stream))
+    return arr
+
+
+def sigma_grouped(jobs, stream=None, graph=False):
+    """jobs: list of (FCI, C, sigma, precision, n_slices, workspace_ptr, workspace_bytes);
+    one fci_sigma_grouped call (split-precision jobs share one contraction launch), or with
+    graph=True fci_sigma_grouped_graph (replayed from a cached CUDA graph for a repeated
+    job list)."""
+    arr = _job_array(jobs)
+    rc = (_sigma_grouped_graph if graph else _sigma_grouped)(arr, len(jobs), _stream(stream))
     if rc:
         raise FCIError(rc, last_error(None) or last_error(jobs[0][0]._h))
+
+
+def clear_grouped_graphs():
+    _clear_grouped_graphs()
 
 
 class DavidsonStepper:

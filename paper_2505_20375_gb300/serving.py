@@ -3,10 +3,12 @@
 Requests (a problem: integrals seed, active space, precision) arrive over time.  A
 request is admitted as soon as a slot is free and its device memory fits the budget;
 its C, sigma and subspace vectors then stay resident until it converges.  Each step,
-the sigma products that all active solves need go to the library in one
-fci_sigma_grouped call (split-precision products with the same slice count share one
-persistent tcgen05 launch), and every solve then takes its Davidson update
-(davidson_advance).  Solves that finish leave the batch and free their memory; waiting
+the sigma products that all active solves need go to the library in one grouped call
+(split-precision products with the same slice count share one persistent tcgen05
+launch), and every solve then takes its Davidson update (davidson_advance).  Each solve
+stages its sigma requests through two fixed vectors (staged_sigma), so while the set of
+active solves and their precisions do not change the grouped call is the same list
+every step and is replayed from a captured CUDA graph (fci_sigma_grouped_graph).  Solves that finish leave the batch and free their memory; waiting
 requests join at the next step.  Reported: time from arrival to converged energy
 (p50/p99) and aggregate determinants * sigma / s.
 
@@ -102,10 +104,12 @@ class Server:
     final_slices: int = 6             # FP64-class correction phase of FCI requests (error < 1e-11
                                       # of ||sigma||); DAS requests correct in FP64
     max_iter: int = 300
+    use_graphs: bool = True           # replay the grouped sigma from captured CUDA graphs
     log: list = field(default_factory=list)
 
     def _opts(self, f: fci.FCI, req: Request):
-        kw = dict(max_iter=self.max_iter, tol_residual=self.tol_residual, tol_energy=self.tol_energy)
+        kw = dict(max_iter=self.max_iter, tol_residual=self.tol_residual, tol_energy=self.tol_energy,
+                  staged_sigma=self.use_graphs)
         if req.mixed and req.kind == "fci" and req.n <= 15:
             return f.davidson_opts(**kw, precision="oz_bf16", n_slices=self.split_slices, switch_residual=1e-4,
                                    final_precision="oz_bf16", final_slices=self.final_slices)
@@ -131,6 +135,11 @@ class Server:
 
     def run(self, requests, clock=time.perf_counter):
         torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(self.device)  # graphs cannot be captured on the legacy stream
+        with torch.cuda.stream(stream):
+            return self._run(requests, clock, stream)
+
+    def _run(self, requests, clock, stream):
         budget = self.memory_budget
         if budget <= 0:
             free, _ = torch.cuda.mem_get_info(self.device)
@@ -141,6 +150,7 @@ class Server:
         t0 = clock()
         det_sigma = 0
         n_steps = 0
+        signatures = set()
         while pending or waiting or active:
             now = clock() - t0
             while pending and pending[0].arrival <= now:
@@ -155,7 +165,7 @@ class Server:
                     f.close()
                     break
                 waiting.pop(0)
-                st = fci.DavidsonStepper(f, opts)
+                st = fci.DavidsonStepper(f, opts, stream=stream)
                 active.append(_Active(req, f, st, clock() - t0, nbytes))
                 used += nbytes
             if not active:
@@ -168,7 +178,8 @@ class Server:
                 x, y, prec, sl, ws, wsb = a.stepper.request()
                 jobs.append((a.f, x, y, prec, sl, ws, wsb))
                 det_sigma += a.f.n_det
-            fci.sigma_grouped(jobs)
+            fci.sigma_grouped(jobs, stream=stream, graph=self.use_graphs)
+            signatures.add(tuple((id(j[0]), j[1], j[2], j[3], j[4], j[5]) for j in jobs))
             n_steps += 1
             still = []
             for a in active:
@@ -192,7 +203,10 @@ class Server:
             "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "converged": int(sum(r.converged for r in results)),
+            "distinct_job_lists": len(signatures),  # graph captures; the other steps replay
         }
+        if self.use_graphs:
+            fci.clear_grouped_graphs()
         return sorted(results, key=lambda r: r.rid), stats
 
 
@@ -201,5 +215,5 @@ def solve_alone(req: Request, server: Server):
     res, _ = Server(device=server.device, max_active=1, memory_budget=server.memory_budget,
                     tol_residual=server.tol_residual, tol_energy=server.tol_energy,
                     split_slices=server.split_slices, final_slices=server.final_slices,
-                    max_iter=server.max_iter).run([Request(**{**req.__dict__, "arrival": 0.0})])
+                    max_iter=server.max_iter, use_graphs=server.use_graphs).run([Request(**{**req.__dict__, "arrival": 0.0})])
     return res[0]

@@ -111,3 +111,64 @@ def test_sigma_graph_replay_matches_direct_call(fci_lib, prec, sl):
             st.synchronize()
             assert torch.equal(got, ref)
     f.clear_graphs()
+
+
+def test_grouped_graph_replays_with_new_vector_contents(fci_lib):
+    """fci_sigma_grouped_graph: the second call with the same job list replays the captured
+    graph; new contents of C give the same results as the plain grouped call, and closing
+    a handle drops the graphs that name it."""
+    probs = [fci_problem(8, 4, 4, seed=21), fci_problem(9, 4, 3, seed=22)]
+    fs = [gpu_fci(p) for p in probs]
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        Cs = [torch.empty(len(p["dets"]), dtype=torch.float64, device="cuda") for p in probs]
+        outs = [torch.empty_like(C) for C in Cs]
+        keep, jobs = [], []
+        for f, C, o, (pr, sl) in zip(fs, Cs, outs, [("oz_bf16", 6), ("fp64", 0)]):
+            nb = f.sigma_workspace_bytes(pr, sl)
+            buf = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+            keep.append(buf)
+            jobs.append((f, C, o, pr, sl, (buf.data_ptr() + 255) & ~255, nb))
+        for seed in (1, 2, 3):
+            for i, C in enumerate(Cs):
+                C.copy_(torch.from_numpy(synth.random_vector(C.numel(), seed=seed + 10 * i)))
+            fci.sigma_grouped(jobs, stream=st, graph=True)
+            got = [o.clone() for o in outs]
+            fci.sigma_grouped(jobs, stream=st)
+            st.synchronize()
+            for g, o in zip(got, outs):
+                assert torch.equal(g, o)
+    fs[1].close()
+    fci.clear_grouped_graphs()
+
+
+def test_staged_stepper_equals_unstaged(fci_lib):
+    """Staging the sigma requests through fixed vectors changes no bit of the solve."""
+    p = fci_problem(8, 4, 4, n_chol=16, seed=3, e_core=0.2)
+    f = gpu_fci(p)
+    res = []
+    for staged in (False, True):
+        st = fci.DavidsonStepper(f, f.davidson_opts(tol_residual=1e-6, tol_energy=1e-10, precision="oz_bf16",
+                                                    n_slices=3, switch_residual=1e-4, final_precision="oz_bf16",
+                                                    final_slices=6, staged_sigma=staged))
+        ptrs = set()
+        while True:
+            x, y, prec, sl, ws, wsb = st.request()
+            ptrs.add((x, y))
+            fci.sigma_grouped([(f, x, y, prec, sl, ws, wsb)])
+            if st.advance():
+                break
+        r = st.finish()
+        res.append((r.energy, len(r.iterations), len(ptrs)))
+    assert res[0][0] == res[1][0] and res[0][1] == res[1][1]
+    assert res[1][2] == 1 and res[0][2] > 1
+
+
+def test_serving_with_graphs_equals_without(fci_lib):
+    reqs = serving.make_requests(8, rate=500.0, seed=11)
+    a, sa = serving.Server(max_active=6, use_graphs=True).run(reqs)
+    b, sb = serving.Server(max_active=6, use_graphs=False).run(reqs)
+    assert sa["converged"] == sb["converged"] == len(reqs)
+    for ra, rb in zip(a, b):
+        assert ra.energy == rb.energy and ra.iterations == rb.iterations
+    assert sa["distinct_job_lists"] < sa["steps"]
