@@ -463,11 +463,12 @@ def run_ours(a, rank, world, local_rank):
         chosen = (tuned or {}).get("chosen", {})
         two_pass = chosen.get("path") == "two-pass gemm"
         products = n_sl * (n_sl + 1) // 2
-        if two_pass:  # bulk-copy GEMM: M = 128 pair rows, K = n_pair_pad rounded to 32, 64-det tiles
-            pad_k = -(-((npair + 15) // 16 * 16) // 32) * 32
+        if two_pass:  # bulk-copy GEMM: M = 128 pair rows, K = n_pair rounded to 16, 64-det tiles
+            pad_k = (npair + 15) // 16 * 16
             bf16_flops = 2.0 * 128 * pad_k * (-(-N // 64) * 64) * products
             kname = f"k_oz_gemm<{n_sl},8> (two-pass: cp.async.bulk-fed tcgen05.mma kind::f16, f16 digit slices)"
-            counted = "executed MMA work: 2 x 128 (pair rows, padded) x K_pad(32) x N_pad(64) x s(s+1)/2"
+            counted = ("executed MMA work: 2 x 128 (pair rows, padded) x K_pad(16) x N_pad(64) x s(s+1)/2 "
+                       "(K padded to 32 when G does not fit in shared memory is not counted)")
         else:  # fused producer kernel: M = 128 pair rows, K = n_pair rounded to 16, NT-det tiles
             pad_k = (npair + 15) // 16 * 16
             bf16_flops = 2.0 * 128 * pad_k * N * products
