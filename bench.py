@@ -143,13 +143,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _kernel_sources_sha() -> str:
-    """Digest of the CUDA sources of the split contraction kernels (the traffic recorded
-    under profiles/ is reported only while these are unchanged)."""
+_KERNEL_SOURCES = {"k_oz_gemm": ("ozaki_gemm.cu", "oz_gemm.cuh", "tc_ptx.cuh"),
+                   "k_oz_contract": ("ozaki.cu", "tc_ptx.cuh")}
+
+
+def _kernel_sources_sha(kernel: str) -> str:
+    """Digest of the CUDA sources of one contraction kernel (the traffic recorded under
+    profiles/ is reported only while these are unchanged)."""
     import hashlib
 
     hsh = hashlib.sha256()
-    for fn in ("ozaki.cu", "ozaki_gemm.cu", "oz_gemm.cuh", "tc_ptx.cuh"):
+    for fn in _KERNEL_SOURCES[kernel.split("<")[0]]:
         with open(os.path.join(ROOT, "paper_2505_20375_gb300", "csrc", fn), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]
@@ -162,7 +166,7 @@ def _traffic_record(kernel: str, workload: str):
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
-    sha = _kernel_sources_sha()
+    sha = _kernel_sources_sha(kernel)
     for line in open(path):
         cells = [c.strip() for c in line.strip().strip("|").split("|")]
         if len(cells) >= 4 and cells[0] == kernel and cells[1] == workload and cells[2] == sha:
