@@ -58,6 +58,9 @@ def _args():
     ap.add_argument("--path", default=None, choices=["fused", "gemm"],
                     help="alpha/beta split path for --profile-case (default: the library's choice)")
     ap.add_argument("--das-electrons", type=int, default=0, help="electrons per spin of a DAS --profile-case")
+    ap.add_argument("--config-davidson", action="store_true",
+                    help="also time Davidson to energy (FP64 vs split forms) on the DAS 16e and 24-spinor configs "
+                         "(minutes: their FP64 sigma takes seconds)")
     return ap.parse_args()
 
 
@@ -427,6 +430,41 @@ def run_ours(a, rank, world, local_rank):
             except Exception as e:  # report, do not abort the benchmark
                 config_runs[name] = {"unavailable": str(e)[:200]}
 
+    # time to energy on the DAS 16e and 24-spinor configs (optional: FP64 solves take minutes)
+    config_dav = None
+    if a.config_davidson and rank == 0:
+        config_dav = {}
+        for name, build, forms in (
+                ("das_16o_4x4_16e_t2", lambda: _build_das(fci, synth, "das_16o_4x4", 8),
+                 (("fp64", dict(precision="fp64")),
+                  ("mixed_s3_then_fp64", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4)))),
+                ("spinor_24s12e", lambda: _build_spinor(fci, synth),
+                 (("fp64", dict(precision="fp64")),
+                  ("oz_s8", dict(precision="oz_bf16", n_slices=8, final_precision="oz_bf16", final_slices=8)),
+                  ("mixed_s3_then_oz_s8", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4,
+                                               final_precision="oz_bf16", final_slices=8))))):
+            row = {}
+            try:
+                fh = build()
+                for form, kw in forms:
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    r = fh.davidson(max_iter=200, tol_residual=1e-5, tol_energy=1e-9, **kw)
+                    torch.cuda.synchronize()
+                    row[form] = {"seconds": time.perf_counter() - t0, "energy": r.energy,
+                                 "iterations": len(r.iterations), "converged": r.converged,
+                                 "sigma_builds": r.n_sigma}
+                e64 = row.get("fp64", {}).get("energy")
+                for form, d in row.items():
+                    if form != "fp64" and e64 is not None:
+                        d["energy_error_vs_fp64"] = abs(d["energy"] - e64)
+                        d["speedup_vs_fp64"] = row["fp64"]["seconds"] / d["seconds"]
+                fh.close()
+                torch.cuda.empty_cache()
+            except Exception as e:
+                row["unavailable"] = str(e)[:200]
+            config_dav[name] = row
+
     # continuous-batching serving: a Poisson stream of Davidson requests (FCI (6e,6o) ..
     # (12e,12o) and 16-orbital 4-space DAS), half of them in mixed precision
     serving_stats = None
@@ -514,6 +552,7 @@ def run_ours(a, rank, world, local_rank):
         "davidson": davidson,
         "serving": serving_stats,
         "configs": config_runs,
+        "config_davidson": config_dav,
         "fp64_peak_tflops_measured": fp64_peak,
     }
     return line

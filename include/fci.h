@@ -168,7 +168,9 @@ typedef struct {
     double tol_residual;    /* ||r|| threshold, default 1e-6 */
     double tol_energy;      /* |dE| threshold, default 1e-10 */
     double eps;             /* compression-compatible preconditioner threshold (Eq.
-                               sparsePreconditioner), default 0 = Davidson's own */
+                               sparsePreconditioner), default 0 = Davidson's own; a
+                               negative value selects 10 / sqrt(N_dets), the largest
+                               threshold the paper found to converge reliably */
     int precision;          /* FCI_PREC_* used for sigma in the first phase */
     int n_slices;           /* slices for FCI_PREC_OZ_BF16 */
     double switch_residual; /* mixed mode: once ||r|| <= this, restart from the Ritz
@@ -178,6 +180,11 @@ typedef struct {
                                FCI_PREC_OZ_BF16 with final_slices >= 6 (error below
                                1e-11 of ||sigma||, the FP64 parity bar) */
     int final_slices;
+    int gap_bound;          /* 1: after convergence, keep the subspace and converge the
+                               second Ritz pair as well, then report the gap lower bound
+                               gamma_0^- = (E_1 - ||r_1||) - E_0 and the energy error bound
+                               ||r_0||^2 / gamma_0^- (Results, eigenvalue bound analysis,
+                               Eq. gammaLowerBound); default 0 */
     int staged_sigma;       /* step-wise ABI: 1 = every sigma request uses the same two
                                vectors of the workspace (x copied in, y copied out by the
                                library), so a caller can replay a captured sigma graph for
@@ -200,6 +207,11 @@ typedef struct {
     int n_sigma;            /* sigma builds performed */
     int capacity;           /* caller sets: length of iters (may be 0 with iters NULL) */
     fci_davidson_iter *iters;
+    /* gap_bound = 1 only (NaN otherwise): the second Ritz value E_1 and its residual norm,
+     * the ground state's residual norm, gamma_0^- and the error bound ||r_0||^2 / gamma_0^-
+     * (+inf if gamma_0^- <= 0), and the iterations spent on the second pair */
+    double e1, r1_norm, r0_norm, gap_lower, error_bound;
+    int gap_iterations;
 } fci_davidson_log;
 
 /* Default options. */

@@ -248,7 +248,9 @@ __global__ void k_hsub_update(double *__restrict__ Hs, const double *__restrict_
 // Lowest eigenpair of the k x k Hermitian Hs (leading dimension KMAX, complex entries)
 // by cyclic Jacobi on the real symmetric embedding of size m = k (real) or 2k (complex).
 // Writes y (complex, k entries) and lam.  One block of 64 threads.
-__global__ void __launch_bounds__(64) k_jacobi(const double *__restrict__ Hs, int k, int cplx,
+// root: 0 = lowest Ritz pair, 1 = second lowest (the real embedding of a complex Hermitian
+// matrix has every eigenvalue twice, so there the selected entry is the (2 root)-th).
+__global__ void __launch_bounds__(64) k_jacobi(const double *__restrict__ Hs, int k, int cplx, int root,
                                                double *__restrict__ y, dav_scalars *__restrict__ out) {
     extern __shared__ double jac_smem[];  // A and Q, each m x (m + 1)
     __shared__ double cs[2];
@@ -322,9 +324,18 @@ __global__ void __launch_bounds__(64) k_jacobi(const double *__restrict__ Hs, in
         }
     }
     if (t == 0) {
+        // the (root * (cplx ? 2 : 1))-th smallest diagonal entry (ties: lowest index)
+        const int want = root * (cplx ? 2 : 1);
         int best = 0;
-        for (int i = 1; i < m; ++i)
-            if (A(i, i) < A(best, best)) best = i;
+        for (int r = 0; r <= want; ++r) {
+            best = -1;
+            for (int i = 0; i < m; ++i) {
+                int rank = 0;  // entries before i in the ascending order
+                for (int j = 0; j < m; ++j)
+                    if (A(j, j) < A(i, i) || (A(j, j) == A(i, i) && j < i)) ++rank;
+                if (rank == r) best = i;
+            }
+        }
         out->lam = A(best, best);
         double nrm = 0.0;
         for (int i = 0; i < k; ++i) {
@@ -400,6 +411,10 @@ struct fci_davidson_state {
     int request = REQ_NONE;
     double *req_x = nullptr, *req_y = nullptr;
     double *stage_x = nullptr, *stage_y = nullptr, *real_y = nullptr;  // staged sigma requests
+    // gap bound (Results, Eq. gammaLowerBound): after convergence, the second Ritz pair
+    bool gap_phase = false;
+    int gap_iters = 0;
+    double E1 = NAN, r1n = NAN, r0n = NAN, gap_lower = NAN, err_bound = NAN;
     std::chrono::steady_clock::time_point t_iter;
     std::vector<fci_davidson_iter> log;
     int status = FCI_OK;
@@ -484,6 +499,7 @@ struct fci_davidson_state {
         vb = (unsigned)std::min<int64_t>(RED_BLOCKS, std::max<int64_t>(1, ceil_div(n, RED_THREADS)));
         prec = o.precision;
         slices = o.n_slices;
+        if (o.eps < 0.0) o.eps = 10.0 / sqrt((double)n);  // the paper's eps <~ 10 / sqrt(N_dets) rule
         final_phase = o.precision == FCI_PREC_FP64 || (o.precision == o.final_precision && o.n_slices == o.final_slices);
         FCI_CUDA(h, cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          2 * (2 * KMAX) * (2 * KMAX + 1) * (int)sizeof(double)));
@@ -537,6 +553,7 @@ struct fci_davidson_state {
         dav_scalars hs{};
         while (!done) {
             if (it >= o.max_iter) {
+                if (gap_phase && (rc = finish_gap())) return rc;  // c back to the ground state
                 done = true;
                 break;
             }
@@ -544,7 +561,8 @@ struct fci_davidson_state {
             t_iter = std::chrono::steady_clock::now();
             {
                 const int m = cplx ? 2 * k : k;
-                k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, y, scal);
+                k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, gap_phase ? 1 : 0, y,
+                                                                          scal);
             }
             FCI_CUDA(h, lincomb(V, k, y, 1.0, c, 0));
             FCI_CUDA(h, lincomb(S, k, y, 1.0, sc, 0));
@@ -569,7 +587,7 @@ struct fci_davidson_state {
             r.max_delta_c = have_prev ? hs.maxdc : 0.0;
             r.residual_norm = rn;
             r.seconds = std::chrono::duration<double>(t1 - t_iter).count();
-            log.push_back(r);
+            if (!gap_phase) log.push_back(r);
             if (!isfinite(lam) || !isfinite(rn)) return fci_fail(h, FCI_ERR_CUDA, "Davidson produced a non-finite value");
             if (!final_phase) {
                 ++phase1_iters;
@@ -583,9 +601,26 @@ struct fci_davidson_state {
                     lam_pending = lam;
                     return ask(REQ_SWITCH, Vk(0), Sk(0));
                 }
+            } else if (gap_phase) {
+                ++gap_iters;
+                E1 = lam;
+                r1n = rn;
+                if (rn <= std::max(o.tol_residual, 0.25 * (lam - E_prev)) || gap_iters >= o.max_iter || k >= ms) {
+                    if ((rc = finish_gap())) return rc;
+                    done = true;
+                    break;
+                }
             } else if (rn <= o.tol_residual && it > 1 && fabs(dE) <= o.tol_energy) {
                 converged = true;
                 E_prev = lam;
+                if (o.gap_bound && k >= 2) {
+                    // keep the subspace and steer it to the second Ritz pair (root 0 stays in it)
+                    gap_phase = true;
+                    have_prev = false;
+                    r0n = rn;
+                    --it;  // the next pass re-diagonalises for root 1 without counting an iteration
+                    continue;
+                }
                 done = true;
                 break;
             }
@@ -593,7 +628,7 @@ struct fci_davidson_state {
                 if (cplx) k_threshold<true><<<vb, RED_THREADS, 0, s>>>(t, n, scal, o.eps);
                 else k_threshold<false><<<vb, RED_THREADS, 0, s>>>(t, n, scal, o.eps);
             }
-            if (k >= ms) {
+            if (k >= ms && !gap_phase) {
                 // collapse to the current and previous Ritz vectors (sigma by linearity)
                 // V_0 = c / ||c||, S_0 = sc / ||c||
                 FCI_CUDA(h, cudaMemcpyAsync(Vk(0), c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
@@ -642,12 +677,17 @@ struct fci_davidson_state {
             k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
             double tn2 = 0.0;
             FCI_CUDA(h, cudaMemcpyAsync(&tn2, nrm, 8, cudaMemcpyDeviceToHost, s));
-            FCI_CUDA(h, cudaMemcpyAsync(cp, c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
-            FCI_CUDA(h, cudaMemcpyAsync(scp, sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            if (!gap_phase) {
+                FCI_CUDA(h, cudaMemcpyAsync(cp, c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                FCI_CUDA(h, cudaMemcpyAsync(scp, sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+            }
             FCI_CUDA(h, cudaStreamSynchronize(s));
-            have_prev = true;
-            E_prev = lam;
+            if (!gap_phase) {
+                have_prev = true;
+                E_prev = lam;
+            }
             if (!(sqrt(tn2) >= 1e-10)) {  // new direction linearly dependent on the subspace
+                if (gap_phase && (rc = finish_gap())) return rc;
                 done = true;
                 break;
             }
@@ -655,6 +695,27 @@ struct fci_davidson_state {
             FCI_CUDA(h, cudaMemcpyAsync(Vk(k), t, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
             return ask(REQ_APPEND, Vk(k), Sk(k));
         }
+        return FCI_OK;
+    }
+
+    // Root 0 on the final subspace (its Ritz vector goes back to c), then the gap bound:
+    // gamma_0^- = (E_1 - ||r_1||) - E_0 and |dE| <= ||r_0||^2 / gamma_0^- (gap theorem).
+    int finish_gap() {
+        dav_scalars hs{};
+        const int m = cplx ? 2 * k : k;
+        k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, 0, y, scal);
+        FCI_CUDA(h, lincomb(V, k, y, 1.0, c, 0));
+        FCI_CUDA(h, lincomb(S, k, y, 1.0, sc, 0));
+        if (cplx) k_residual<true><<<vb, RED_THREADS, 0, s>>>(c, sc, cp, false, diag, scal, n, t, partial);
+        else k_residual<false><<<vb, RED_THREADS, 0, s>>>(c, sc, cp, false, diag, scal, n, t, partial);
+        k_reduce_residual<<<1, 32, 0, s>>>(partial, vb, scal);
+        FCI_CUDA(h, cudaGetLastError());
+        FCI_CUDA(h, cudaMemcpyAsync(&hs, scal, sizeof hs, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(h, cudaStreamSynchronize(s));
+        E_prev = hs.lam;
+        r0n = sqrt(hs.rnorm2);
+        gap_lower = (E1 - r1n) - E_prev;
+        err_bound = gap_lower > 0.0 ? r0n * r0n / gap_lower : INFINITY;
         return FCI_OK;
     }
 
@@ -669,6 +730,12 @@ struct fci_davidson_state {
             lg->n_iter = lg->iters ? m : 0;
             lg->converged = converged ? 1 : 0;
             lg->n_sigma = n_sigma;
+            lg->e1 = E1;
+            lg->r1_norm = r1n;
+            lg->r0_norm = r0n;
+            lg->gap_lower = gap_lower;
+            lg->error_bound = err_bound;
+            lg->gap_iterations = gap_iters;
         }
         if (!converged)
             return fci_fail(h, FCI_ERR_NOT_CONVERGED, "Davidson did not converge in %d iterations", o.max_iter);

@@ -540,14 +540,15 @@ void fci_davidson_default_opts(fci_davidson_opts *o) {
     o->final_precision = FCI_PREC_FP64;
     o->final_slices = 0;
     o->staged_sigma = 0;
+    o->gap_bound = 0;
 }
 
 static int check_opts(fci_context *h, const fci_davidson_opts *o) {
     if (!o) return fci_fail(h, FCI_ERR_ARG, "NULL opts");
     if (o->max_iter < 1 || o->max_subspace < 2 || o->max_subspace > 32)
         return fci_fail(h, FCI_ERR_ARG, "max_iter >= 1 and max_subspace in [2, 32] required");
-    if (!(o->tol_residual > 0) || !(o->tol_energy > 0) || !(o->eps >= 0))
-        return fci_fail(h, FCI_ERR_ARG, "tolerances must be positive, eps >= 0");
+    if (!(o->tol_residual > 0) || !(o->tol_energy > 0) || !(o->eps == o->eps))
+        return fci_fail(h, FCI_ERR_ARG, "tolerances must be positive, eps a number");
     if (o->precision != FCI_PREC_FP64 && o->precision != FCI_PREC_OZ_BF16)
         return fci_fail(h, FCI_ERR_ARG, "unknown precision %d", o->precision);
     if (o->precision == FCI_PREC_OZ_BF16 && (o->n_slices < 2 || o->n_slices > 8))

@@ -410,7 +410,12 @@ __global__ void k_to_fixed(const double *__restrict__ C, int64_t n, int s,
         Cint[i] = __double2ll_rn(scalbn(C[i], sh));
 }
 
-__global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, int npair, int log2T,
+// sigma_I = scale * sum over the replacements of I of sign * E_int[pq, K] + e_core C_I, in
+// int64.  Thread = beta string ib (consecutive threads, consecutive determinants), looping
+// over alpha strings; pairs are taken 8 at a time, their 16 table entries loaded first,
+// then their 16 E_int values, so that each thread keeps 16 loads in flight.  Pair-table
+// rows run to n_pair_pad (multiple of 16) and hold -1 past n_pair.
+__global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, int npair_pad, int log2T,
                                                      const int32_t *__restrict__ pairA,
                                                      const int32_t *__restrict__ pairB,
                                                      const int64_t *__restrict__ E, int64_t ldE,
@@ -428,18 +433,27 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
     for (int64_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
         const int64_t det = ia * nsb + ib;
         int64_t acc = 0;
-        for (int pp = 0; pp < npair; ++pp) {
-            const int32_t ea = __ldg(pairA + (int64_t)pp * nsa + ia);
-            if (ea >= 0) {
-                const int64_t K = (int64_t)(ea >> 1) * nsb + ib;
-                const int64_t e = __ldg(E + (K >> log2T) * tstride + ((int64_t)pp << log2T) + (K & tmask));
-                acc += (ea & 1) ? -e : e;
+        for (int p0 = 0; p0 < npair_pad; p0 += 8) {
+            int32_t ea[8], eb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                ea[e] = __ldg(pairA + (int64_t)(p0 + e) * nsa + ia);
+                eb[e] = __ldg(pairB + (int64_t)(p0 + e) * nsb + ib);
             }
-            const int32_t eb = __ldg(pairB + (int64_t)pp * nsb + ib);
-            if (eb >= 0) {
-                const int64_t K = ia * nsb + (eb >> 1);
-                const int64_t e = __ldg(E + (K >> log2T) * tstride + ((int64_t)pp << log2T) + (K & tmask));
-                acc += (eb & 1) ? -e : e;
+            int64_t xa[8], xb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t Ka = ea[e] >= 0 ? (int64_t)(ea[e] >> 1) * nsb + ib : 0;
+                const int64_t Kb = eb[e] >= 0 ? ia * nsb + (eb[e] >> 1) : 0;
+                const int64_t row = ea[e] >= 0 ? (int64_t)(p0 + e) << log2T : 0;
+                const int64_t rowb = eb[e] >= 0 ? (int64_t)(p0 + e) << log2T : 0;
+                xa[e] = __ldg(E + (Ka >> log2T) * tstride + row + (Ka & tmask));
+                xb[e] = __ldg(E + (Kb >> log2T) * tstride + rowb + (Kb & tmask));
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                acc += ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa[e] : xa[e]);
+                acc += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb[e] : xb[e]);
             }
         }
         sigma[det] = bad ? __longlong_as_double(0x7FF8000000000000ll) : scalbn(__ll2double_rn(acc), u) + e_core * C[det];
@@ -494,7 +508,7 @@ __global__ void __launch_bounds__(64 * KCC) k_fci_split(int64_t ndet, int64_t ns
 #pragma unroll
             for (int e = 0; e < 8; e += 2)
                 w[e / 2] = j < 4 ? digits_f16x2(ylo[e], ylo[e + 1], sel) : digits_f16x2(yhi[e], yhi[e + 1], sel);
-            *(uint4 *)(base + j * B_PLANE) = make_uint4(w[0], w[1], w[2], w[3]);
+            __stcs((uint4 *)(base + j * B_PLANE), make_uint4(w[0], w[1], w[2], w[3]));  // streaming: keep C_int in L2
         }
     }
 }
@@ -737,8 +751,8 @@ static int oz_finish_job(fci_context *h, const double *C, double *sigma, const O
     phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
     const int threads = 128;
     dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
-    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, prm.nt == 32 ? 5 : 6, h->d_pair_a, h->d_pair_b, E,
-                                       prm.npair,
+    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair_pad, prm.nt == 32 ? 5 : 6, h->d_pair_a, h->d_pair_b,
+                                       E, prm.npair,
                                        C, h->e_core,
                                        8 * prm.L0 - h->G_exp, shC, status, sigma);
     FCI_CUDA(h, cudaGetLastError());
@@ -808,7 +822,7 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
     phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
     const int threads = 128;
     dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
-    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair, 6, h->d_pair_a, h->d_pair_b, E, OZG_M, C,
+    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair_pad, 6, h->d_pair_a, h->d_pair_b, E, OZG_M, C,
                                        h->e_core, 8 * oz_gemm_L0(s, 8) - h->G_exp, shC, status, sigma);
     FCI_CUDA(h, cudaGetLastError());
     return FCI_OK;

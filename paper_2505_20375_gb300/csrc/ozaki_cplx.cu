@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) k_cz_split(int n, int64_t ndet, int n_kc,
             w.y = digits7_f16x2(y[2], y[3], j);
             w.z = digits7_f16x2(y[4], y[5], j);
             w.w = digits7_f16x2(y[6], y[7], j);
-            *(uint4 *)(base + j * CZ_B_PLANE) = w;
+            __stcs((uint4 *)(base + j * CZ_B_PLANE), w);  // streaming: keep C_int in L2
         }
     }
 }

@@ -46,7 +46,8 @@ class fci_info(ctypes.Structure):
 class fci_davidson_opts(ctypes.Structure):
     _fields_ = [("max_iter", _i32), ("max_subspace", _i32), ("tol_residual", _dbl), ("tol_energy", _dbl),
                 ("eps", _dbl), ("precision", _i32), ("n_slices", _i32), ("switch_residual", _dbl),
-                ("use_guess", _i32), ("final_precision", _i32), ("final_slices", _i32), ("staged_sigma", _i32)]
+                ("use_guess", _i32), ("final_precision", _i32), ("final_slices", _i32), ("gap_bound", _i32),
+                ("staged_sigma", _i32)]
 
 
 class fci_davidson_iter(ctypes.Structure):
@@ -56,7 +57,8 @@ class fci_davidson_iter(ctypes.Structure):
 
 class fci_davidson_log(ctypes.Structure):
     _fields_ = [("n_iter", _i32), ("converged", _i32), ("n_sigma", _i32), ("capacity", _i32),
-                ("iters", ctypes.POINTER(fci_davidson_iter))]
+                ("iters", ctypes.POINTER(fci_davidson_iter)), ("e1", _dbl), ("r1_norm", _dbl), ("r0_norm", _dbl),
+                ("gap_lower", _dbl), ("error_bound", _dbl), ("gap_iterations", _i32)]
 
 
 def _sig(name, args, res=_i32):
@@ -128,6 +130,12 @@ def last_error(h=None) -> str:
     return (_last_error(h) or b"").decode()
 
 
+def _gap_of(log) -> dict:
+    if log.gap_iterations <= 0 and log.e1 != log.e1:  # NaN: no gap phase
+        return None
+    return {k: getattr(log, k) for k in ("e1", "r1_norm", "r0_norm", "gap_lower", "error_bound", "gap_iterations")}
+
+
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     return _vp(s.cuda_stream)
@@ -150,6 +158,7 @@ class DavidsonResult:
     converged: bool
     n_sigma: int
     iterations: list
+    gap: dict = None  # gap_bound: e1, r1_norm, r0_norm, gap_lower, error_bound, gap_iterations
 
 
 class FCI:
@@ -292,7 +301,7 @@ class FCI:
 
     def davidson_opts(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                       precision="fp64", n_slices=6, switch_residual=1e-5, final_precision="fp64", final_slices=0,
-                      use_guess=False, staged_sigma=False) -> fci_davidson_opts:
+                      use_guess=False, staged_sigma=False, gap_bound=False) -> fci_davidson_opts:
         o = fci_davidson_opts()
         _dav_defaults(ctypes.byref(o))
         o.max_iter, o.max_subspace = max_iter, max_subspace
@@ -301,6 +310,7 @@ class FCI:
         o.final_precision, o.final_slices = PRECISIONS[final_precision], final_slices
         o.use_guess = 1 if use_guess else 0
         o.staged_sigma = 1 if staged_sigma else 0
+        o.gap_bound = 1 if gap_bound else 0
         return o
 
     def davidson_workspace_bytes(self, opts: fci_davidson_opts) -> int:
@@ -310,7 +320,7 @@ class FCI:
 
     def davidson(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                  precision="fp64", n_slices=6, switch_residual=1e-5, guess: torch.Tensor = None,
-                 final_precision="fp64", final_slices=0, stream=None) -> DavidsonResult:
+                 final_precision="fp64", final_slices=0, gap_bound=False, stream=None) -> DavidsonResult:
         o = fci_davidson_opts()
         _dav_defaults(ctypes.byref(o))
         o.max_iter, o.max_subspace = max_iter, max_subspace
@@ -318,6 +328,7 @@ class FCI:
         o.precision, o.n_slices, o.switch_residual = PRECISIONS[precision], n_slices, switch_residual
         o.use_guess = 1 if guess is not None else 0
         o.final_precision, o.final_slices = PRECISIONS[final_precision], final_slices
+        o.gap_bound = 1 if gap_bound else 0
         b = _sz()
         self._check(_dav_ws(self._h, ctypes.byref(o), ctypes.byref(b)))
         p, nb = self._workspace(b.value)
@@ -332,7 +343,7 @@ class FCI:
         if rc not in (FCI_OK, FCI_ERR_NOT_CONVERGED):
             self._check(rc)
         its = [{k: getattr(iters[i], k) for k, _ in fci_davidson_iter._fields_} for i in range(log.n_iter)]
-        return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its)
+        return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its, _gap_of(log))
 
     def sync_status(self, stream=None):
         """Synchronise and raise FCIError(FCI_ERR_TIMEOUT) if a device wait expired."""
@@ -430,4 +441,4 @@ class DavidsonStepper:
         if rc not in (FCI_OK, FCI_ERR_NOT_CONVERGED):
             self.f._check(rc)
         its = [{k: getattr(iters[i], k) for k, _ in fci_davidson_iter._fields_} for i in range(log.n_iter)]
-        return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its)
+        return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its, _gap_of(log))
