@@ -336,7 +336,9 @@ def run_ours(a, rank, world, local_rank):
                  ("oz_s7", dict(precision="oz_bf16", n_slices=7, final_precision="oz_bf16", final_slices=7)),
                  ("mixed_s3_then_oz_s7", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4,
                                               final_precision="oz_bf16", final_slices=7)),
-                 ("mixed_s3_then_fp64", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4)))
+                 ("mixed_s3_then_fp64", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4)),
+                ("oz_s7_gap_bound", dict(precision="oz_bf16", n_slices=7, final_precision="oz_bf16",
+                                         final_slices=7, gap_bound=True)))
         for name, kw in forms:
             try:
                 torch.cuda.synchronize()
@@ -347,6 +349,8 @@ def run_ours(a, rank, world, local_rank):
                                   "iterations": len(r.iterations), "sigma_builds": r.n_sigma,
                                   "converged": r.converged,
                                   "final_residual": r.iterations[-1]["residual_norm"] if r.iterations else None}
+                if r.gap is not None:  # gap theorem: |dE| <= ||r_0||^2 / gamma_0^-
+                    davidson[name]["gap"] = r.gap
             except fci.FCIError as e:
                 davidson[name] = {"unavailable": str(e)[:200]}
         e64 = davidson.get("fp64", {}).get("energy")
@@ -437,7 +441,9 @@ def run_ours(a, rank, world, local_rank):
         for name, build, forms in (
                 ("das_16o_4x4_16e_t2", lambda: _build_das(fci, synth, "das_16o_4x4", 8),
                  (("fp64", dict(precision="fp64")),
-                  ("mixed_s3_then_fp64", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4)))),
+                  ("mixed_s3_then_fp64", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4)),
+                ("oz_s7_gap_bound", dict(precision="oz_bf16", n_slices=7, final_precision="oz_bf16",
+                                         final_slices=7, gap_bound=True)))),
                 ("spinor_24s12e", lambda: _build_spinor(fci, synth),
                  (("fp64", dict(precision="fp64")),
                   ("oz_s8", dict(precision="oz_bf16", n_slices=8, final_precision="oz_bf16", final_slices=8)),
