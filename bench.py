@@ -150,6 +150,22 @@ _KERNEL_SOURCES = {"k_oz_gemm": ("ozaki_gemm.cu", "oz_gemm.cuh", "tc_ptx.cuh"),
                    "k_oz_contract": ("ozaki.cu", "tc_ptx.cuh")}
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of `values` over the ranks of the default process group (the
+    slowest rank's times)."""
+    import torch
+
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return t.tolist()
+
+
+def replica_throughput(world: int, n_det: int, steps: int, seconds: float) -> float:
+    """Whole-job determinants * sigma / s of `world` replicas that each ran `steps` sigma
+    builds of `n_det` determinants, timed by the slowest rank (weak scaling)."""
+    return world * n_det * steps / seconds
+
+
 def _kernel_sources_sha(kernel: str) -> str:
     """Digest of the CUDA sources of one contraction kernel (the traffic recorded under
     profiles/ is reported only while these are unchanged)."""
@@ -487,14 +503,11 @@ def run_ours(a, rank, world, local_rank):
         serving_stats["p50_mixed_s"] = float(np.percentile(mixed, 50)) if mixed else None
         serving_stats["p50_fp64_s"] = float(np.percentile(plain, 50)) if plain else None
 
-    # max over ranks
+    # max over ranks (replicas: every rank ran the same workload)
     if world > 1:
-        t = torch.tensor([T, T_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        T, T_e2e = t.tolist()
-
-    value = world * N * a.steps / T
-    e2e = world * N * a.steps / T_e2e
+        T, T_e2e = max_over_ranks([T, T_e2e], dev)
+    value = replica_throughput(world, N, a.steps, T)
+    e2e = replica_throughput(world, N, a.steps, T_e2e)
     # roofline of the dominant kernel (the contraction)
     ph = phases["contract"]
     npair = f.info["n_pair"]
