@@ -462,53 +462,57 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
 
 // Two-pass path, first pass: the digit image of D for the bulk-copy GEMM.  Block (N-tile
 // nt, K-chunk kc) holds S planes of 64 determinants x 8 KCC pairs in canonical K-major
-// core matrices; one CTA of 64 KCC threads fills one block, thread t covering determinant
-// t % 64 and pairs 8 (t / 64) .. 8 (t / 64) + 7 of the chunk (pair-table rows past
-// n_pair_pad and determinants past the end give zero digits).
+// core matrices; one CTA of 64 KCC threads fills every K-chunk of one N-tile, thread t
+// covering determinant t % 64 (decoded once) and pairs 8 (t / 64) .. 8 (t / 64) + 7 of each
+// chunk (pair-table rows past n_pair_pad and determinants past the end give zero digits).
 template <int S, int KCC>
 __global__ void __launch_bounds__(64 * KCC) k_fci_split(int64_t ndet, int64_t nsa, int64_t nsb, int npair_pad, int n_kc,
-                                                        int64_t n_blocks, const int32_t *__restrict__ pairA,
+                                                        int64_t n_nt, const int32_t *__restrict__ pairA,
                                                         const int32_t *__restrict__ pairB,
                                                         const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
     constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
     constexpr int B_PLANE = OZG_N * KCC * 16;
     const int row = threadIdx.x & 63, cc = threadIdx.x >> 6;
     const uint32_t nsb32 = (uint32_t)nsb;
-    for (int64_t blk = blockIdx.x; blk < n_blocks; blk += gridDim.x) {
-        const int64_t nt = blk / n_kc;
-        const int kc = (int)(blk - nt * n_kc);
+    for (int64_t nt = blockIdx.x; nt < n_nt; nt += gridDim.x) {
+        // this thread's determinant, decoded once for every K-chunk of the tile
         const uint32_t det = (uint32_t)(nt * OZG_N + row);
         const bool live = det < (uint64_t)ndet;
         const uint32_t ka = live ? det / nsb32 : 0u, kb = live ? det - ka * nsb32 : 0u;
         const int64_t *Crow = Cint + (int64_t)ka * nsb;
-        int32_t ea[8], eb[8];
+        const int32_t *pa = pairA + ka, *pb = pairB + kb;
+        uint8_t *tile = Dimg + (size_t)nt * n_kc * S * B_PLANE + ((row >> 3) * KCC + cc) * 128 + (row & 7) * 16;
+#pragma unroll 1
+        for (int kc = 0; kc < n_kc; ++kc) {
+            int32_t ea[8], eb[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int rs = kc * 8 * KCC + cc * 8 + e;
-            const bool ok = live && rs < npair_pad;
-            ea[e] = ok ? __ldg(pairA + (int64_t)rs * nsa + ka) : -1;
-            eb[e] = ok ? __ldg(pairB + (int64_t)rs * nsb + kb) : -1;
-        }
-        uint32_t ylo[8], yhi[8];
+            for (int e = 0; e < 8; ++e) {
+                const int rs = kc * 8 * KCC + cc * 8 + e;
+                const bool ok = live && rs < npair_pad;
+                ea[e] = ok ? __ldg(pa + (int64_t)rs * nsa) : -1;
+                eb[e] = ok ? __ldg(pb + (int64_t)rs * nsb) : -1;
+            }
+            uint32_t ylo[8], yhi[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int64_t xa = __ldg(Cint + (int64_t)(ea[e] >= 0 ? (ea[e] >> 1) : 0) * nsb + kb);
-            const int64_t xb = __ldg(Crow + (eb[e] >= 0 ? (eb[e] >> 1) : 0));
-            int64_t v = ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa : xa);
-            v += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb : xb);
-            const uint64_t y = (uint64_t)v + bias;
-            ylo[e] = (uint32_t)y;
-            yhi[e] = (uint32_t)(y >> 32);
-        }
-        uint8_t *base = Dimg + (size_t)blk * S * B_PLANE + ((row >> 3) * KCC + cc) * 128 + (row & 7) * 16;
+            for (int e = 0; e < 8; ++e) {
+                const int64_t xa = __ldg(Cint + (int64_t)(ea[e] >= 0 ? (ea[e] >> 1) : 0) * nsb + kb);
+                const int64_t xb = __ldg(Crow + (eb[e] >= 0 ? (eb[e] >> 1) : 0));
+                int64_t v = ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa : xa);
+                v += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb : xb);
+                const uint64_t y = (uint64_t)v + bias;
+                ylo[e] = (uint32_t)y;
+                yhi[e] = (uint32_t)(y >> 32);
+            }
+            uint8_t *base = tile + (size_t)kc * S * B_PLANE;
 #pragma unroll
-        for (int j = 0; j < S; ++j) {
-            const uint32_t bj = (uint32_t)(j & 3), sel = bj | ((4u + bj) << 8);
-            uint32_t w[4];
+            for (int j = 0; j < S; ++j) {
+                const uint32_t bj = (uint32_t)(j & 3), sel = bj | ((4u + bj) << 8);
+                uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 8; e += 2)
-                w[e / 2] = j < 4 ? digits_f16x2(ylo[e], ylo[e + 1], sel) : digits_f16x2(yhi[e], yhi[e + 1], sel);
-            __stcs((uint4 *)(base + j * B_PLANE), make_uint4(w[0], w[1], w[2], w[3]));  // streaming: keep C_int in L2
+                for (int e = 0; e < 8; e += 2)
+                    w[e / 2] = j < 4 ? digits_f16x2(ylo[e], ylo[e + 1], sel) : digits_f16x2(yhi[e], yhi[e + 1], sel);
+                __stcs((uint4 *)(base + j * B_PLANE), make_uint4(w[0], w[1], w[2], w[3]));  // streaming: keep C_int in L2
+            }
         }
     }
 }
@@ -793,12 +797,11 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
         const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(N, 256), 152 * 8);
         k_absmax_bits<<<nb, 256, 0, st>>>(C, N, maxbits);
         k_to_fixed<<<nb, 256, 0, st>>>(C, N, s, maxbits, Cint, shC);
-        const int64_t nblk = n_nt * n_kc;
-        const unsigned gb = (unsigned)std::min<int64_t>(nblk, 152 * 16);
+        const unsigned gb = (unsigned)std::min<int64_t>(n_nt, 152 * 16);
         switch (s * 10 + tg.kcc) {
 #define OZ_SPLIT(S_, K_)                                                                                          \
     case S_ * 10 + K_:                                                                                            \
-        k_fci_split<S_, K_><<<gb, 64 * K_, 0, st>>>(N, h->nsa, h->nsb, h->npair_pad, n_kc, nblk, h->d_pair_a,      \
+        k_fci_split<S_, K_><<<gb, 64 * K_, 0, st>>>(N, h->nsa, h->nsb, h->npair_pad, n_kc, n_nt, h->d_pair_a,      \
                                                    h->d_pair_b, Cint, Dimg);                                      \
         break;
             OZ_SPLIT(2, 2) OZ_SPLIT(3, 2) OZ_SPLIT(4, 2) OZ_SPLIT(5, 2) OZ_SPLIT(6, 2) OZ_SPLIT(7, 2)
