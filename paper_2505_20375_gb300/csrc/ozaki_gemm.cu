@@ -5,9 +5,11 @@
 //              s level accumulators and commits;
 //   warps 2..  epilogue: 8 warps (two per TMEM lane quadrant, 32 columns each) when the
 //              accumulators are double-buffered (s <= 4), else 16 (four per quadrant,
-//              16 columns each), which for s <= 6 load all levels of their columns
-//              into registers and release the accumulator before combining.
-// Level accumulators are double-buffered when 2 s x 64 TMEM columns fit in 512.  Work units
+//              16 columns each), which read the levels three at a time and release each
+//              group as soon as it is in registers.
+// Level accumulators are double-buffered when 2 s x 64 TMEM columns fit in 512; otherwise
+// the first K-chunk of a unit issues the MMAs of each level group once the epilogue has
+// released it.  Work units
 // are (N-tile, M-tile) pairs, N-tile outer and dealt round-robin, so the M-tiles of one
 // B tile run at about the same time and its reads hit L2.  Every mbarrier wait is bounded
 // in time (FCI_ERR_TIMEOUT in the status word on expiry; the kernel drains the MMAs it
@@ -52,14 +54,16 @@ struct OzgParams {
 
 struct OzgShared {
     uint64_t full[OZG_MAX_STAGES], empty[OZG_MAX_STAGES];
-    uint64_t acc_full[2], acc_empty[2];
+    uint64_t acc_full[2], acc_empty[3];  // acc_empty: per buffer, or per level group (one buffer)
     uint64_t drain, a_full;
     uint32_t tmem_base;
     int abort;
 };
 
+template <bool FAST = false>
 __device__ __forceinline__ bool ozg_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                         long long timeout) {
+    if (FAST && mbar_test_wait(bar, parity)) return true;
     const long long t0 = clock64();
     int spins = 0;
     while (!mbar_try_wait_sleep(bar, parity)) {
@@ -75,10 +79,11 @@ __device__ __forceinline__ bool ozg_wait(uint32_t bar, uint32_t parity, volatile
     return true;
 }
 
+template <bool FAST = false>
 __device__ __forceinline__ bool ozg_wait_warp(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                              long long timeout) {
     int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = ozg_wait(bar, parity, abort, status, timeout) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = ozg_wait<FAST>(bar, parity, abort, status, timeout) ? 1 : 0;
     return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
 }
 
@@ -87,6 +92,11 @@ __device__ __forceinline__ bool ozg_wait_warp(uint32_t bar, uint32_t parity, vol
 template <int S, int W, int KCC, bool RESA>
 __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_constant__ OzgParams p) {
     constexpr int NBUF = (2 * S * OZG_N <= 512) ? 2 : 1;
+    // With one accumulator buffer the epilogue releases the levels in groups of GH as it
+    // reads them, and the next unit's first K-chunk issues each group's MMAs once that
+    // group is free.
+    constexpr int GH = 3;
+    constexpr int NG = NBUF == 1 ? (S + GH - 1) / GH : 1;
     constexpr int L0 = oz_gemm_L0(S, W);
     constexpr uint32_t A_PLANE = OZG_M * KCC * 16, B_PLANE = OZG_N * KCC * 16;
     constexpr uint32_t STAGE_A = S * A_PLANE, STAGE_B = S * B_PLANE;
@@ -104,10 +114,8 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
             mbar_init(smem_u32(&sh->full[r]), 1);
             mbar_init(smem_u32(&sh->empty[r]), 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&sh->acc_full[b]), 1);
-            mbar_init(smem_u32(&sh->acc_empty[b]), ozg_epi_warps(S));
-        }
+        for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&sh->acc_full[b]), 1);
+        for (int b = 0; b < 3; ++b) mbar_init(smem_u32(&sh->acc_empty[b]), ozg_epi_warps(S));
         mbar_init(smem_u32(&sh->drain), 1);
         mbar_init(smem_u32(&sh->a_full), 1);
         sh->abort = 0;
@@ -133,7 +141,7 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
                 for (uint32_t o = 0; o < total; o += 32768u)
                     bulk_g2s(smem_u32(sA + o), p.Gimg + o, total - o < 32768u ? total - o : 32768u, ab);
             }
-            uint32_t q = 0;
+            uint32_t q = 0, st = 0, ph = 0;  // stage counter, its ring slot and the slot's use parity
             for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x) {
                 const int64_t nt = u / p.n_mt;
                 const int mt = (int)(u - nt * p.n_mt);
@@ -141,10 +149,8 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
                 const uint8_t *gb = p.Dimg + (size_t)nt * p.n_kc * STAGE_B;
                 bool ok = true;
                 for (int kc = 0; kc < p.n_kc; ++kc, ++q) {
-                    const int st = (int)(q % (uint32_t)R);
-                    const uint32_t use = q / (uint32_t)R;
-                    if (use > 0 && !ozg_wait(smem_u32(&sh->empty[st]), (use - 1) & 1, abort, p.status,
-                                            p.timeout_cycles)) {
+                    if (q >= (uint32_t)R &&
+                        !ozg_wait<true>(smem_u32(&sh->empty[st]), ph ^ 1, abort, p.status, p.timeout_cycles)) {
                         ok = false;
                         break;
                     }
@@ -152,6 +158,10 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
                     mbar_expect_tx(fb, STAGE_LOAD);
                     if (!RESA) bulk_g2s(smem_u32(sA + (size_t)st * STAGE_A), ga + (size_t)kc * STAGE_A, STAGE_A, fb);
                     bulk_g2s(smem_u32(sB + (size_t)st * STAGE_B), gb + (size_t)kc * STAGE_B, STAGE_B, fb);
+                    if (++st == (uint32_t)R) {
+                        st = 0;
+                        ph ^= 1;
+                    }
                 }
                 if (!ok) break;
             }
@@ -159,43 +169,74 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------------------ MMA issuer
+            // The ring slot and its parity advance with each stage (no division on the
+            // issue path), and each wait first tests the barrier without blocking.
+            auto wait = [&](uint32_t bar, uint32_t par) -> bool {
+                return ozg_wait<true>(bar, par, abort, p.status, p.timeout_cycles);
+            };
             const uint32_t idesc = idesc_f16(OZG_M, OZG_N);
             const uint64_t a0 = smem_desc(smem_u32(sA), 128, KCC * 128);
             const uint64_t b0 = smem_desc(smem_u32(sB), 128, KCC * 128);
-            uint32_t q = 0, tau = 0;
+            uint32_t st = 0, ph = 0, tau = 0;  // ring slot, its use parity, unit counter
             bool issued = false, ok = true;
-            if (RESA && !ozg_wait(smem_u32(&sh->a_full), 0, abort, p.status, p.timeout_cycles)) ok = false;
+            if (RESA && !wait(smem_u32(&sh->a_full), 0)) ok = false;
             for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++tau) {
                 const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
-                if (tau >= (uint32_t)NBUF) {
-                    const uint32_t par = NBUF == 2 ? ((tau >> 1) - 1) & 1 : (tau - 1) & 1;
-                    if (!ozg_wait(smem_u32(&sh->acc_empty[buf]), par, abort, p.status, p.timeout_cycles)) break;
+                if (NBUF == 2 && tau >= 2) {
+                    if (!wait(smem_u32(&sh->acc_empty[buf]), ((tau >> 1) - 1) & 1)) break;
+                    tc_fence_after();
                 }
-                tc_fence_after();
                 const uint32_t dbase = tmem + (uint32_t)(buf * S * OZG_N);
-                for (int kc = 0; kc < p.n_kc; ++kc, ++q) {
-                    const int st = (int)(q % (uint32_t)R);
-                    if (!ozg_wait(smem_u32(&sh->full[st]), (q / (uint32_t)R) & 1, abort, p.status, p.timeout_cycles)) {
+                for (int kc = 0; kc < p.n_kc; ++kc) {
+                    if (!wait(smem_u32(&sh->full[st]), ph)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t as = a0 + (uint64_t)(((RESA ? kc : st) * STAGE_A) >> 4);
+                    const uint64_t as = a0 + (uint64_t)(((RESA ? kc : (int)st) * STAGE_A) >> 4);
                     const uint64_t bs = b0 + (uint64_t)((st * STAGE_B) >> 4);
+                    // the MMAs of this K-chunk whose level lies in [lo, hi)
+                    auto issue = [&](int lo, int hi) {
 #pragma unroll
-                    for (int kk = 0; kk < KCC / 2; ++kk) {
+                        for (int kk = 0; kk < KCC / 2; ++kk) {
 #pragma unroll
-                        for (int j = S - 1; j >= 0; --j) {
-                            const uint64_t b = bs + (uint64_t)((j * B_PLANE + kk * 256) >> 4);
-                            const uint32_t acc_in = (kc != 0 || kk != 0 || j != S - 1) ? 1u : 0u;
+                            for (int j = S - 1; j >= 0; --j) {
+                                const uint64_t b = bs + (uint64_t)((j * B_PLANE + kk * 256) >> 4);
+                                const uint32_t acc_in = (kc != 0 || kk != 0 || j != S - 1) ? 1u : 0u;
 #pragma unroll
-                            for (int i = S - 1 - j; i < S; ++i)
-                                mma_f16(dbase + (uint32_t)((i + j - (S - 1)) * OZG_N),
-                                        as + (uint64_t)((i * A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
+                                for (int i = S - 1 - j; i < S; ++i) {
+                                    const int lv = i + j - (S - 1);
+                                    if (lv >= lo && lv < hi)
+                                        mma_f16(dbase + (uint32_t)(lv * OZG_N),
+                                                as + (uint64_t)((i * A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
+                                }
+                            }
                         }
+                    };
+                    if (NBUF == 1 && kc == 0 && tau >= 1) {
+                        bool freed = true;
+#pragma unroll
+                        for (int g = 0; g < NG; ++g) {
+                            if (!wait(smem_u32(&sh->acc_empty[g]), (tau - 1) & 1)) {
+                                freed = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            issue(g * GH, g * GH + GH);
+                        }
+                        if (!freed) {
+                            ok = false;
+                            break;
+                        }
+                    } else {
+                        issue(0, S);
                     }
                     issued = true;
                     mma_commit(smem_u32(&sh->empty[st]));
+                    if (++st == (uint32_t)R) {
+                        st = 0;
+                        ph ^= 1;
+                    }
                 }
                 if (!ok) break;
                 mma_commit(smem_u32(&sh->acc_full[buf]));
@@ -213,17 +254,17 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
         }
     } else {
         // ---------------------------------------------------------------- epilogue
-        // Warp (quadrant qd, part) owns lanes 32 qd .. 32 qd + 31 and columns
-        // 16 part .. 16 part + 15.  For s <= 6 every level of those columns fits in
-        // registers: the warp loads them all, hands the accumulator back to the MMA warp at
-        // once (so the next unit's MMAs overlap this unit's combination and stores), then
-        // combines.  For larger s it combines level by level and releases at the end.
+        // Warp (quadrant qd, part) owns lanes 32 qd .. 32 qd + 31 and 16 CH columns from
+        // 16 CH part.  Single-buffered accumulators (s >= 5, CH = 1) are read GH levels at a
+        // time; each group is handed back to the MMA warp as soon as it is in registers, so
+        // the next unit's first K-chunk starts on it while the rest is read and combined.
+        // Double-buffered accumulators (s <= 4, CH = 2) are combined level by level and
+        // released at the end.
         constexpr int CH = OZG_N / (4 * ozg_epi_warps(S));  // 16-column chunks per warp: 2 or 1
         const int qd = warp & 3;
         const int cw = 16 * CH * ((warp - 2) >> 2);
         const int row = 32 * qd + lane;
         constexpr int lowshift = W * (L0 - (S - 1));
-        constexpr bool EARLY = NBUF == 1 && S <= 6;
         uint32_t tau = 0;
         for (int64_t u = blockIdx.x; u < n_units; u += gridDim.x, ++tau) {
             const int64_t nt = u / p.n_mt;
@@ -235,39 +276,41 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
             const uint32_t tl0 = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * OZG_N + cw);
             int64_t *dst0 = p.E + ((size_t)nt * p.M_pad + (size_t)mt * OZG_M + row) * OZG_N + cw;
             const bool keep = mt * OZG_M + row < p.M_real;  // rows past the operator's size are never read
-            if (EARLY) {  // CH == 1
-                const uint32_t tl = tl0;
-                int64_t *dst = dst0;
-                uint32_t vs[S][16];
+            if (NBUF == 1) {  // CH == 1: group by group, each released as soon as it is read
+                auto term = [](uint32_t x, int L) -> int64_t {
+                    const int64_t v = (int64_t)__float2int_rn(__uint_as_float(x));
+                    return L < L0 ? v * ((int64_t)1 << (W * (L - (S - 1)))) : v * ((int64_t)1 << (W * (L - L0)));
+                };
+                int64_t acc[16];
 #pragma unroll
-                for (int l = 0; l < S; ++l) tmem_ld16(tl + (uint32_t)(l * OZG_N), vs[l]);
-                tmem_ld_wait();
+                for (int c = 0; c < 16; ++c) acc[c] = 0;
 #pragma unroll
-                for (int l = 0; l < S; ++l) tmem_regs_ready(vs[l]);
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
+                for (int g = 0; g < NG; ++g) {
+                    uint32_t v[GH][16];
 #pragma unroll
-                for (int c = 0; c < 16; c += 2) {
-                    int64_t a[2] = {0, 0};
+                    for (int l = g * GH; l < g * GH + GH && l < S; ++l) tmem_ld16(tl0 + (uint32_t)(l * OZG_N), v[l - g * GH]);
+                    tmem_ld_wait();
 #pragma unroll
-                    for (int h = 0; h < 2; ++h)
+                    for (int l = g * GH; l < g * GH + GH && l < S; ++l) tmem_regs_ready(v[l - g * GH]);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[g]));
 #pragma unroll
-                        for (int L = S - 1; L <= 2 * S - 2; ++L) {
-                            const int64_t v = (int64_t)__float2int_rn(__uint_as_float(vs[L - (S - 1)][c + h]));
-                            if (L < L0) {
-                                a[h] += v * ((int64_t)1 << (W * (L - (S - 1))));
-                            } else {
-                                if (L == L0 && lowshift > 0)
-                                    a[h] = (a[h] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
-                                a[h] += v * ((int64_t)1 << (W * (L - L0)));
-                            }
+                    for (int l = g * GH; l < g * GH + GH && l < S; ++l) {
+                        const int L = S - 1 + l;
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            if (L == L0 && lowshift > 0)
+                                acc[c] = (acc[c] + ((int64_t)1 << (lowshift > 0 ? lowshift - 1 : 0))) >> lowshift;
+                            acc[c] += term(v[l - g * GH][c], L);
                         }
-                    if (keep) __stcs((longlong2 *)(dst + c), make_longlong2(a[0], a[1]));
+                    }
                 }
+                if (keep)
+#pragma unroll
+                    for (int c = 0; c < 16; c += 2) __stcs((longlong2 *)(dst0 + c), make_longlong2(acc[c], acc[c + 1]));
             } else {
-                // combine level by level; with one chunk per warp (single-buffered
-                // accumulators) release before the stores, with two (double-buffered) after
+                // double-buffered accumulators: combine level by level, release at the end
 #pragma unroll 1
                 for (int ch = 0; ch < CH; ++ch) {
                     int64_t acc[16];
@@ -294,21 +337,14 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
                                 acc[c] += (int64_t)__float2int_rn(__uint_as_float(v[c])) * ((int64_t)1 << (W * (L - L0)));
                         }
                     }
-                    if (CH == 1) {
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
-                    }
                     if (keep)
 #pragma unroll
                         for (int c = 0; c < 16; c += 2)
                             __stcs((longlong2 *)(dst0 + 16 * ch + c), make_longlong2(acc[c], acc[c + 1]));
                 }
-                if (CH != 1) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
-                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sh->acc_empty[buf]));
             }
         }
     }

@@ -27,6 +27,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Non-blocking test of the phase with the given parity.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Same test, but a thread whose phase is not complete may be suspended (up to the hint,
 // in ns) instead of returning at once, so waiting warps stop competing for issue slots.
 __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t a, uint32_t parity) {
