@@ -415,47 +415,52 @@ __global__ void k_to_fixed(const double *__restrict__ C, int64_t n, int s,
 // over alpha strings; pairs are taken 8 at a time, their 16 table entries loaded first,
 // then their 16 E_int values, so that each thread keeps 16 loads in flight.  Pair-table
 // rows run to n_pair_pad (multiple of 16) and hold -1 past n_pair.
-__global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, int npair_pad, int log2T,
+__global__ void __launch_bounds__(256) k_scatter_int(uint32_t nsa, uint32_t nsb, int npair_pad, int log2T,
                                                      const int32_t *__restrict__ pairA,
                                                      const int32_t *__restrict__ pairB,
                                                      const int64_t *__restrict__ E, int64_t ldE,
                                                      const double *__restrict__ C, double e_core, int ushift,
                                                      const int *__restrict__ shC, const int *__restrict__ status,
                                                      double *__restrict__ sigma) {
-    const int64_t ib = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const uint32_t ib = blockIdx.x * blockDim.x + threadIdx.x;
     if (ib >= nsb) return;
     const int u = ushift - *shC;
     const bool bad = *status != 0;
     // E is tile-major: element (pq, K) at (K / T) * R * T + pq * T + K % T, T = 2^log2T,
-    // R = ldE rows per tile (n_pair for the fused kernel, 128 for the two-pass GEMM)
-    const int64_t tstride = ldE << log2T;
-    const int64_t tmask = ((int64_t)1 << log2T) - 1;
-    for (int64_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
-        const int64_t det = ia * nsb + ib;
+    // R = ldE rows per tile (n_pair for the fused kernel, 128 for the two-pass GEMM).
+    // Determinant indices are 32-bit (ndet < 2^31); a pair-table entry e is 2 x (source
+    // string) + (1 if odd) or -1, and ((x & valid) ^ odd) - odd with valid = ~(e >> 31),
+    // odd = -(e & 1) gives +x, -x or 0 (absent entries load a valid element, then drop it).
+    const uint64_t tstride = (uint64_t)ldE << log2T;
+    const uint32_t tmask = (1u << log2T) - 1u;
+    for (uint32_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
+        const uint32_t rowoff = ia * nsb;
+        const int32_t *pa = pairA + ia, *pb = pairB + ib;
         int64_t acc = 0;
-        for (int p0 = 0; p0 < npair_pad; p0 += 8) {
+        for (int p0 = 0; p0 < npair_pad; p0 += 8, pa += 8 * nsa, pb += 8 * nsb) {
             int32_t ea[8], eb[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                ea[e] = __ldg(pairA + (int64_t)(p0 + e) * nsa + ia);
-                eb[e] = __ldg(pairB + (int64_t)(p0 + e) * nsb + ib);
+                ea[e] = __ldg(pa + e * nsa);
+                eb[e] = __ldg(pb + e * nsb);
             }
             int64_t xa[8], xb[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int64_t Ka = ea[e] >= 0 ? (int64_t)(ea[e] >> 1) * nsb + ib : 0;
-                const int64_t Kb = eb[e] >= 0 ? ia * nsb + (eb[e] >> 1) : 0;
-                const int64_t row = ea[e] >= 0 ? (int64_t)(p0 + e) << log2T : 0;
-                const int64_t rowb = eb[e] >= 0 ? (int64_t)(p0 + e) << log2T : 0;
-                xa[e] = __ldg(E + (Ka >> log2T) * tstride + row + (Ka & tmask));
-                xb[e] = __ldg(E + (Kb >> log2T) * tstride + rowb + (Kb & tmask));
+                const uint32_t Ka = (uint32_t)max(ea[e] >> 1, 0) * nsb + ib;
+                const uint32_t Kb = rowoff + (uint32_t)max(eb[e] >> 1, 0);
+                const uint32_t r = (uint32_t)(p0 + e) << log2T;
+                xa[e] = __ldg(E + ((uint64_t)(Ka >> log2T) * tstride + (r + (Ka & tmask))));
+                xb[e] = __ldg(E + ((uint64_t)(Kb >> log2T) * tstride + (r + (Kb & tmask))));
             }
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                acc += ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa[e] : xa[e]);
-                acc += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb[e] : xb[e]);
+                const int64_t va = ~(int64_t)(ea[e] >> 31), oa = -(int64_t)(ea[e] & 1);
+                const int64_t vb = ~(int64_t)(eb[e] >> 31), ob = -(int64_t)(eb[e] & 1);
+                acc += (((xa[e] & va) ^ oa) - oa) + (((xb[e] & vb) ^ ob) - ob);
             }
         }
+        const uint32_t det = rowoff + ib;
         sigma[det] = bad ? __longlong_as_double(0x7FF8000000000000ll) : scalbn(__ll2double_rn(acc), u) + e_core * C[det];
     }
 }
@@ -465,40 +470,47 @@ __global__ void __launch_bounds__(256) k_scatter_int(int64_t nsa, int64_t nsb, i
 // core matrices; one CTA of 64 KCC threads fills every K-chunk of one N-tile, thread t
 // covering determinant t % 64 (decoded once) and pairs 8 (t / 64) .. 8 (t / 64) + 7 of each
 // chunk (pair-table rows past n_pair_pad and determinants past the end give zero digits).
+// Index arithmetic is 32-bit (the caller guarantees ndet < 2^31), and the sign is
+// branch-free: an entry e of a pair table is 2 x (source string) + (1 if the excitation is
+// odd), or -1 for none; ((x & valid) ^ odd) - odd with valid = ~(e >> 31) and
+// odd = -(e & 1) gives +x, -x or 0 (the load index of an absent entry is clamped to a
+// valid element).
 template <int S, int KCC>
-__global__ void __launch_bounds__(64 * KCC) k_fci_split(int64_t ndet, int64_t nsa, int64_t nsb, int npair_pad, int n_kc,
-                                                        int64_t n_nt, const int32_t *__restrict__ pairA,
+__global__ void __launch_bounds__(64 * KCC) k_fci_split(uint32_t ndet, uint32_t nsa, uint32_t nsb, int npair_pad,
+                                                        int n_kc, int64_t n_nt, const int32_t *__restrict__ pairA,
                                                         const int32_t *__restrict__ pairB,
                                                         const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
     constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
     constexpr int B_PLANE = OZG_N * KCC * 16;
     const int row = threadIdx.x & 63, cc = threadIdx.x >> 6;
-    const uint32_t nsb32 = (uint32_t)nsb;
     for (int64_t nt = blockIdx.x; nt < n_nt; nt += gridDim.x) {
         // this thread's determinant, decoded once for every K-chunk of the tile
         const uint32_t det = (uint32_t)(nt * OZG_N + row);
-        const bool live = det < (uint64_t)ndet;
-        const uint32_t ka = live ? det / nsb32 : 0u, kb = live ? det - ka * nsb32 : 0u;
-        const int64_t *Crow = Cint + (int64_t)ka * nsb;
-        const int32_t *pa = pairA + ka, *pb = pairB + kb;
+        const bool live = det < ndet;
+        const uint32_t ka = live ? det / nsb : 0u, kb = live ? det - ka * nsb : 0u;
+        const uint32_t rowoff = ka * nsb;
+        const int32_t *pa = pairA + ((uint32_t)(cc * 8) * nsa + ka);
+        const int32_t *pb = pairB + ((uint32_t)(cc * 8) * nsb + kb);
+        const uint32_t stepa = 8u * KCC * nsa, stepb = 8u * KCC * nsb;
         uint8_t *tile = Dimg + (size_t)nt * n_kc * S * B_PLANE + ((row >> 3) * KCC + cc) * 128 + (row & 7) * 16;
 #pragma unroll 1
-        for (int kc = 0; kc < n_kc; ++kc) {
+        for (int kc = 0; kc < n_kc; ++kc, pa += stepa, pb += stepb) {
+            const int rs0 = kc * 8 * KCC + cc * 8;
             int32_t ea[8], eb[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int rs = kc * 8 * KCC + cc * 8 + e;
-                const bool ok = live && rs < npair_pad;
-                ea[e] = ok ? __ldg(pa + (int64_t)rs * nsa) : -1;
-                eb[e] = ok ? __ldg(pb + (int64_t)rs * nsb) : -1;
+                const bool ok = live && rs0 + e < npair_pad;
+                ea[e] = ok ? __ldg(pa + e * nsa) : -1;
+                eb[e] = ok ? __ldg(pb + e * nsb) : -1;
             }
             uint32_t ylo[8], yhi[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int64_t xa = __ldg(Cint + (int64_t)(ea[e] >= 0 ? (ea[e] >> 1) : 0) * nsb + kb);
-                const int64_t xb = __ldg(Crow + (eb[e] >= 0 ? (eb[e] >> 1) : 0));
-                int64_t v = ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa : xa);
-                v += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb : xb);
+                const int64_t xa = __ldg(Cint + ((uint32_t)max(ea[e] >> 1, 0) * nsb + kb));
+                const int64_t xb = __ldg(Cint + (rowoff + (uint32_t)max(eb[e] >> 1, 0)));
+                const int64_t va = ~(int64_t)(ea[e] >> 31), oa = -(int64_t)(ea[e] & 1);
+                const int64_t vb = ~(int64_t)(eb[e] >> 31), ob = -(int64_t)(eb[e] & 1);
+                const int64_t v = (((xa & va) ^ oa) - oa) + (((xb & vb) ^ ob) - ob);
                 const uint64_t y = (uint64_t)v + bias;
                 ylo[e] = (uint32_t)y;
                 yhi[e] = (uint32_t)(y >> 32);
@@ -678,6 +690,7 @@ static int oz_prepare_Gt(fci_context *h, int s) {
 static int oz_prepare_job(fci_context *h, const double *C, int s, void *ws, cudaStream_t st, OzParams &prm,
                           int64_t **E_out, int **shC_out, int **status_out) {
     if (h->mode != FCI_MODE_FCI) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision needs alpha/beta strings");
+    if (h->ndet >= ((int64_t)1 << 31)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision: 2^31 determinants or more");
     int rc = oz_prepare_G(h, s);
     if (rc) return rc;
     const int KC = oz_kc(h);
@@ -771,6 +784,7 @@ static int oz_num_sms(fci_context *h, int *nsm) {
 // Two-pass split sigma: fixed point, D digit image (k_fci_split), bulk-copy GEMM (8-bit
 // digits, one M-tile of 128 pair rows), integer scatter.
 static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int s, void *ws, cudaStream_t st) {
+    if (h->ndet >= ((int64_t)1 << 31)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision: 2^31 determinants or more");
     int rc = oz_prepare_Gt(h, s);
     if (rc) return rc;
     const OzTwoPass tg = oz_gemm_geom(h, s);
@@ -801,8 +815,8 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
         switch (s * 10 + tg.kcc) {
 #define OZ_SPLIT(S_, K_)                                                                                          \
     case S_ * 10 + K_:                                                                                            \
-        k_fci_split<S_, K_><<<gb, 64 * K_, 0, st>>>(N, h->nsa, h->nsb, h->npair_pad, n_kc, n_nt, h->d_pair_a,      \
-                                                   h->d_pair_b, Cint, Dimg);                                      \
+        k_fci_split<S_, K_><<<gb, 64 * K_, 0, st>>>((uint32_t)N, (uint32_t)h->nsa, (uint32_t)h->nsb, h->npair_pad,  \
+                                                   n_kc, n_nt, h->d_pair_a, h->d_pair_b, Cint, Dimg);             \
         break;
             OZ_SPLIT(2, 2) OZ_SPLIT(3, 2) OZ_SPLIT(4, 2) OZ_SPLIT(5, 2) OZ_SPLIT(6, 2) OZ_SPLIT(7, 2)
             OZ_SPLIT(2, 4) OZ_SPLIT(3, 4) OZ_SPLIT(4, 4) OZ_SPLIT(5, 4) OZ_SPLIT(6, 4) OZ_SPLIT(7, 4)
