@@ -103,6 +103,7 @@ struct OzShared {  // lives after the operand buffers
 // Bounded wait: returns false on timeout or when another role has aborted.
 __device__ __forceinline__ bool oz_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                         long long timeout) {
+    if (mbar_test_wait(bar, parity)) return true;  // usually complete already: no clock read
     const long long t0 = clock64();
     int spins = 0;
     while (!mbar_try_wait_sleep(bar, parity)) {
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
         const int t = threadIdx.x;  // 0..223
         const int units = NT * KC;
         constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
-        uint32_t q = 0;
+        uint32_t q = 0, slot = 0, ph = 0;  // planes produced, ring slot, the slot's use parity
         for (int64_t tile = t_begin; tile < t_end; ++tile) {
             uint32_t ylo[UNITS][8], yhi[UNITS][8];
 #pragma unroll
@@ -207,22 +208,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
                 // determinant counts of the split path fit 32 bits (n <= 15 orbitals)
                 const uint32_t det = (uint32_t)tile * NT + (uint32_t)r;
                 const bool live = unit < units && det < (uint32_t)p.N;
-                const uint32_t nsb = (uint32_t)p.nsb;
+                const uint32_t nsa = (uint32_t)p.nsa, nsb = (uint32_t)p.nsb;
                 const uint32_t ka = live ? det / nsb : 0u, kb = live ? det - ka * nsb : 0u;
-                const int64_t *Crow = p.Cint + (int64_t)ka * nsb;
+                const uint32_t rowoff = ka * nsb;
+                const int32_t *pa = p.pairA + ((uint32_t)(8 * c) * nsa + ka);
+                const int32_t *pb = p.pairB + ((uint32_t)(8 * c) * nsb + kb);
                 int32_t ea[8], eb[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const int rs = 8 * c + e;
-                    ea[e] = live ? __ldg(p.pairA + (int64_t)rs * p.nsa + ka) : -1;
-                    eb[e] = live ? __ldg(p.pairB + (int64_t)rs * p.nsb + kb) : -1;
+                    ea[e] = live ? __ldg(pa + e * nsa) : -1;
+                    eb[e] = live ? __ldg(pb + e * nsb) : -1;
                 }
+                // entry e = 2 x (source string) + odd, or -1: ((x & valid) ^ odd) - odd is
+                // +x, -x or 0 (absent entries load a clamped, valid element)
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const int64_t xa = __ldg(p.Cint + (int64_t)(ea[e] >= 0 ? (ea[e] >> 1) : 0) * p.nsb + kb);
-                    const int64_t xb = __ldg(Crow + (eb[e] >= 0 ? (eb[e] >> 1) : 0));
-                    int64_t v = ea[e] < 0 ? 0 : ((ea[e] & 1) ? -xa : xa);
-                    v += eb[e] < 0 ? 0 : ((eb[e] & 1) ? -xb : xb);
+                    const int64_t xa = __ldg(p.Cint + ((uint32_t)max(ea[e] >> 1, 0) * nsb + kb));
+                    const int64_t xb = __ldg(p.Cint + (rowoff + (uint32_t)max(eb[e] >> 1, 0)));
+                    const int64_t va = ~(int64_t)(ea[e] >> 31), oa = -(int64_t)(ea[e] & 1);
+                    const int64_t vb = ~(int64_t)(eb[e] >> 31), ob = -(int64_t)(eb[e] & 1);
+                    const int64_t v = (((xa & va) ^ oa) - oa) + (((xb & vb) ^ ob) - ob);
                     const uint64_t y = (uint64_t)v + bias;
                     ylo[u][e] = (uint32_t)y;
                     yhi[u][e] = (uint32_t)(y >> 32);
@@ -230,10 +235,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
             }
 #pragma unroll
             for (int j = S - 1; j >= 0; --j, ++q) {
-                const int slot = q % RING;
-                const uint32_t use = q / RING;
-                if (use > 0 && !oz_wait_warp(smem_u32(&sh->plane_empty[slot]), (use - 1) & 1, abort, p.status,
-                                             p.timeout_cycles))
+                if (q >= (uint32_t)RING && !oz_wait_warp(smem_u32(&sh->plane_empty[slot]), ph ^ 1, abort, p.status,
+                                                         p.timeout_cycles))
                     goto producer_done;
                 uint8_t *plane = sRing + slot * plane_bytes;
                 const uint32_t bj = (uint32_t)(j & 3);
@@ -254,6 +257,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0 && !p.stall_test) mbar_arrive(smem_u32(&sh->plane_full[slot]));
+                if (++slot == (uint32_t)RING) {
+                    slot = 0;
+                    ph ^= 1;
+                }
             }
         }
     producer_done:;
@@ -335,7 +342,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
         const uint64_t bdesc0 = smem_desc(smem_u32(sRing), 128, sbo);
         const uint32_t bstep = (uint32_t)(plane_bytes >> 4);  // ring slots are contiguous
         const int ksteps = KC / 2;
-        uint32_t q = 0, tau = 0;
+        uint32_t slot = 0, ph = 0, tau = 0;  // ring slot, its use parity, tile counter
         bool issued = false;
         for (int64_t tile = t_begin; tile < t_end; ++tile, ++tau) {
             const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
@@ -347,10 +354,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
             const uint32_t dbase = tmem + (uint32_t)(buf * S * NT);
             bool ok = true;
 #pragma unroll
-            for (int j = S - 1; j >= 0; --j, ++q) {
-                const int slot = q % RING;
-                if (!oz_wait(smem_u32(&sh->plane_full[slot]), (q / RING) & 1, abort, p.status,
-                             p.timeout_cycles)) {
+            for (int j = S - 1; j >= 0; --j) {
+                if (!oz_wait(smem_u32(&sh->plane_full[slot]), ph, abort, p.status, p.timeout_cycles)) {
                     ok = false;
                     break;
                 }
@@ -366,6 +371,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
                 }
                 issued = true;
                 mma_commit(smem_u32(&sh->plane_empty[slot]));
+                if (++slot == (uint32_t)RING) {
+                    slot = 0;
+                    ph ^= 1;
+                }
             }
             if (!ok) break;
             mma_commit(smem_u32(&sh->acc_full[buf]));
