@@ -181,10 +181,13 @@ typedef struct {
                                1e-11 of ||sigma||, the FP64 parity bar) */
     int final_slices;
     int gap_bound;          /* 1: after convergence, keep the subspace and converge the
-                               second Ritz pair as well, then report the gap lower bound
-                               gamma_0^- = (E_1 - ||r_1||) - E_0 and the energy error bound
-                               ||r_0||^2 / gamma_0^- (Results, eigenvalue bound analysis,
-                               Eq. gammaLowerBound); default 0 */
+                               second Ritz pair as well (until ||r_1|| <= max(tol_residual,
+                               (E_1 - E_0) / 4) or max_iter further steps; a full subspace
+                               restarts from the ground state and the second Ritz vector),
+                               then report the gap lower bound gamma_0^- = (E_1 - ||r_1||)
+                               - E_0 and the energy error bound ||r_0||^2 / gamma_0^-
+                               (Results, eigenvalue bound analysis, Eq. gammaLowerBound);
+                               default 0 */
     int staged_sigma;       /* step-wise ABI: 1 = every sigma request uses the same two
                                vectors of the workspace (x copied in, y copied out by the
                                library), so a caller can replay a captured sigma graph for

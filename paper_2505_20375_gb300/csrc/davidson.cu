@@ -552,12 +552,11 @@ struct fci_davidson_state {
         int rc;
         dav_scalars hs{};
         while (!done) {
-            if (it >= o.max_iter) {
-                if (gap_phase && (rc = finish_gap())) return rc;  // c back to the ground state
+            if (!gap_phase && it >= o.max_iter) {
                 done = true;
                 break;
             }
-            ++it;
+            if (!gap_phase) ++it;  // second-root passes have their own limit (max_iter of them)
             t_iter = std::chrono::steady_clock::now();
             {
                 const int m = cplx ? 2 * k : k;
@@ -605,7 +604,8 @@ struct fci_davidson_state {
                 ++gap_iters;
                 E1 = lam;
                 r1n = rn;
-                if (rn <= std::max(o.tol_residual, 0.25 * (lam - E_prev)) || gap_iters >= o.max_iter || k >= ms) {
+                if (rn <= std::max(o.tol_residual, 0.25 * (lam - E_prev)) || gap_iters >= o.max_iter ||
+                    (k >= ms && ms < 3)) {
                     if ((rc = finish_gap())) return rc;
                     done = true;
                     break;
@@ -618,8 +618,7 @@ struct fci_davidson_state {
                     gap_phase = true;
                     have_prev = false;
                     r0n = rn;
-                    --it;  // the next pass re-diagonalises for root 1 without counting an iteration
-                    continue;
+                    continue;  // the next pass re-diagonalises for root 1
                 }
                 done = true;
                 break;
@@ -666,6 +665,40 @@ struct fci_davidson_state {
                 for (int jj = 0; jj < knew; ++jj)
                     if ((rc = add_column(jj))) return rc;
                 k = knew;
+            }
+            if (k >= ms && gap_phase) {
+                // collapse to the ground-state Ritz vector (it must stay in the subspace for
+                // the final E_0) and the current second Ritz vector orthogonalised against it;
+                // c_prev / sc_prev are free in this phase and hold the ground state meanwhile
+                {
+                    const int m = cplx ? 2 * k : k;
+                    k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, 0, y, scal);
+                }
+                FCI_CUDA(h, lincomb(V, k, y, 1.0, cp, 0));
+                FCI_CUDA(h, lincomb(S, k, y, 1.0, scp, 0));
+                FCI_CUDA(h, cudaMemcpyAsync(Vk(0), cp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                FCI_CUDA(h, cudaMemcpyAsync(Sk(0), scp, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, partial);
+                k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+                k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, nrm);
+                k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(0), nreal, nrm);
+                FCI_CUDA(h, cudaMemcpyAsync(Vk(1), c, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                FCI_CUDA(h, cudaMemcpyAsync(Sk(1), sc, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
+                for (int pass = 0; pass < 2; ++pass) {
+                    FCI_CUDA(h, multidot(Vk(0), 1, Vk(1), dots));
+                    k_negate<<<1, 64, 0, s>>>(dots, 1);
+                    FCI_CUDA(h, lincomb(Vk(0), 1, dots, 1.0, Vk(1), 1));
+                    FCI_CUDA(h, lincomb(Sk(0), 1, dots, 1.0, Sk(1), 1));
+                }
+                k_norm2<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, partial);
+                k_reduce_norm<<<1, 32, 0, s>>>(partial, vb, nrm);
+                k_scale<<<vb, RED_THREADS, 0, s>>>(Vk(1), nreal, nrm);
+                k_scale<<<vb, RED_THREADS, 0, s>>>(Sk(1), nreal, nrm);
+                FCI_CUDA(h, cudaGetLastError());
+                FCI_CUDA(h, cudaMemsetAsync(Hs, 0, 2 * KMAX * KMAX * 8, s));
+                for (int jj = 0; jj < 2; ++jj)
+                    if ((rc = add_column(jj))) return rc;
+                k = 2;
             }
             // two rounds of classical Gram-Schmidt against V[0..k)
             for (int round = 0; round < 2; ++round) {

@@ -59,6 +59,22 @@ def test_gap_bound_das(fci_lib):
     _check(r, np.linalg.eigvalsh(oracle.dense_h(hso, gso, dets).real))
 
 
+@pytest.mark.parametrize("ms", [3, 4])
+def test_gap_bound_restarts(fci_lib, ms):
+    """A small subspace fills up during the second-root phase: it restarts from the ground
+    state and the current second Ritz vector and goes on until the second residual is
+    below a quarter of the gap, so the bound is finite and holds."""
+    p = fci_problem(8, 4, 4, n_chol=16, seed=1, e_core=0.25)
+    f = gpu_fci(p)
+    r = f.davidson(tol_residual=1e-6, tol_energy=1e-10, gap_bound=True, max_subspace=ms)
+    H = oracle.dense_h(p["hso"], p["gso"], p["dets"]).real
+    evals = np.linalg.eigvalsh(H)
+    _check(r, evals, 0.25)
+    assert r.gap["gap_iterations"] >= 2
+    assert r.gap["r1_norm"] <= 0.25 * (r.gap["e1"] - r.energy) * (1 + 1e-9)
+    assert np.isfinite(r.gap["error_bound"])
+
+
 def test_no_gap_phase_by_default(fci_lib):
     p = fci_problem(6, 3, 3)
     f = gpu_fci(p)
