@@ -24,14 +24,16 @@
 // address of a connected determinant is a table lookup, one block offset per
 // (alpha pattern, beta pattern) held in shared memory, and a multiply-add.
 //
-// Kernel layout (one persistent CTA per SM, 544 threads):
-//   warps 0-7   producers: decode the tile's determinants (category, strings, local
-//               indices) once per tile, then per K-chunk gather D_int for 128
-//               determinants x 8 KCH pairs from C_int and write its s digit planes;
-//   warps 8-15  epilogue: per TMEM lane quadrant two warps split the N columns, read the
-//               s levels in chunks of 16, combine in int64, store E (FP32, pair-major
-//               inside each tile of 128 determinants);
-//   warp 16     allocates TMEM; lane 0 issues the MMAs and the commits.
+// Kernel layout (one persistent CTA per SM, 672 threads; PW = 8 or 12 producer warps as
+// tuned):
+//   warps 0 .. PW-1       producers: decode the tile's determinants (category, strings,
+//                         local indices) once per tile, then per K-chunk gather D_int for
+//                         128 determinants x 8 KCH pairs from C_int and write its s digit
+//                         planes;
+//   warps PW .. 19        epilogue: per TMEM lane quadrant (20 - PW) / 4 warps take its
+//                         16-column chunks in turn, read the s levels, combine in int64,
+//                         store E (FP32, pair-major inside each tile of 128 determinants);
+//   warp 20               allocates TMEM; lane 0 issues the MMAs and the commits.
 // Tiles are dealt round-robin to the CTAs of a job, so at any time the CTAs work on
 // neighbouring determinants and share the rows of C they gather (L2 locality).
 // Waits on mbarriers are bounded in time as in the alpha/beta kernel.
@@ -51,8 +53,10 @@ using namespace tc;
 using das_dev::find_cat;
 
 constexpr int DZ_TILE = 128;  // determinants per tile (the MMA's M)
-constexpr int DZ_EPILOGUE_WARPS = 4;  // one per TMEM lane quadrant
-__host__ __device__ constexpr int dz_threads(int pw) { return 32 * (pw + DZ_EPILOGUE_WARPS + 1); }
+// Epilogue warps: the CTA keeps 21 warps (96 registers per thread), so 8 epilogue warps
+// (two per TMEM lane quadrant) beside 12 producers and 12 (three per quadrant) beside 8.
+__host__ __device__ constexpr int dz_epi_warps(int pw) { return 20 - pw; }
+__host__ __device__ constexpr int dz_threads(int pw) { return 32 * (pw + dz_epi_warps(pw) + 1); }
 constexpr int DZ_MAX_RING = 4;
 constexpr int DZ_LOC_BITS = 22;  // packed replacement entry: ((pattern << 22 | local) << 1) | sign
 constexpr int32_t DZ_LOC_MASK = (1 << DZ_LOC_BITS) - 1;
@@ -96,6 +100,7 @@ struct DzShared {
 
 __device__ __forceinline__ bool dz_wait(uint32_t bar, uint32_t parity, volatile int *abort, int *status,
                                         long long timeout) {
+    if (mbar_test_wait(bar, parity)) return true;  // usually complete already: no clock read
     const long long t0 = clock64();
     int spins = 0;
     while (!mbar_try_wait_sleep(bar, parity)) {
@@ -119,8 +124,8 @@ __device__ __forceinline__ bool dz_wait_warp(uint32_t bar, uint32_t parity, vola
 }
 
 // S: slices per operand; KCH: K-cores (8 pairs each) per ring slot, 2, 4 or 6;
-// PW: producer warps (8 or 12; KCH a multiple of PW / 4).  Warps PW .. PW+3 run the
-// epilogue, warp PW+4 the MMAs.
+// PW: producer warps (8 or 12; KCH a multiple of PW / 4).  Warps PW .. 19 run the
+// epilogue (20 - PW of them, evenly over the TMEM lane quadrants), warp 20 the MMAs.
 template <int S, int KCH, int PW>
 __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_constant__ DzGroup grp) {
     __shared__ DzParams p;
@@ -135,7 +140,8 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
     __syncthreads();
     constexpr int HG = PW / 4;            // producer threads per determinant
     constexpr int UNITS = KCH / HG;       // K-cores per producer thread per chunk
-    constexpr int EW = DZ_EPILOGUE_WARPS;
+    constexpr int EW = dz_epi_warps(PW);
+    static_assert(EW % 4 == 0 && PW % 4 == 0, "epilogue warps must cover the TMEM lane quadrants evenly");
     constexpr int DZ_MMA_WARP = PW + EW;
     static_assert(KCH % HG == 0, "K-chunk not divisible among the producer threads");
     extern __shared__ __align__(1024) uint8_t dz_smem_raw[];
@@ -204,7 +210,8 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
         const int npb = p.n_pat_b;
         int32_t *sRow = sRowAll + warp * npb;
         const int32_t nla = (int32_t)p.nla, nlb = (int32_t)p.nlb;
-        uint32_t q = 0;
+        const int32_t zero2 = (int32_t)(2 * p.n_det);  // the zero pair of the signed C values
+        uint32_t q = 0, slot = 0, ph = 0;  // chunks produced, ring slot, the slot's use parity
         for (int64_t tile = cta; tile < ntiles; tile += cta_n) {
             const int64_t off = tile * DZ_TILE + r;
             const bool live = off < p.len;
@@ -242,8 +249,9 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
 #pragma unroll
                 for (int u = 0; u < UNITS; ++u) {
                     const int gc = ch * KCH + hg + HG * u;
+                    // signed C values: C2[2 K] = +C_K, C2[2 K + 1] = -C_K, C2[2 n_det] = 0, so a
+                    // move (target K, sign bit) reads C2[2 K + sign] and an absent one reads 0
                     int32_t Ka[8], Kb[8];
-                    uint32_t sgn = 0;  // bit e: alpha sign, bit 8 + e: beta sign
                     if (uni) {
                         // lane e < 8 resolves the alpha move of pair 8 gc + e for the warp's
                         // alpha string (lane 0's), as (target row offset << 1) | sign
@@ -261,11 +269,9 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
                             const int32_t a = __shfl_sync(0xFFFFFFFFu, ab, e);
-                            Ka[e] = (a >= 0 && live) ? (a >> 1) + lb : -1;
-                            sgn |= (uint32_t)(a & 1) << e;
-                            const int32_t rb = eb[e] >= 0 ? sRow[eb[e] >> 23] : -1;
-                            Kb[e] = rb >= 0 ? rb + ((eb[e] >> 1) & DZ_LOC_MASK) : -1;
-                            sgn |= (uint32_t)(eb[e] & 1) << (8 + e);
+                            Ka[e] = (a >= 0 && live) ? a + 2 * lb : zero2;
+                            const int32_t rb = sRow[max(eb[e] >> 23, 0)];
+                            Kb[e] = (eb[e] >= 0 && rb >= 0) ? 2 * rb + (eb[e] & 0x7FFFFF) : zero2;
                         }
                     } else {
                         int32_t ea[8], eb[8];
@@ -276,30 +282,20 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
                         }
 #pragma unroll
                         for (int e = 0; e < 8; ++e) {
-                            const int32_t ba = ea[e] >= 0 ? bA[(ea[e] >> 23) * npb] : -1;
-                            const int32_t bb = eb[e] >= 0 ? bB[eb[e] >> 23] : -1;
-                            Ka[e] = ba >= 0 ? ba + ((ea[e] >> 1) & DZ_LOC_MASK) * nb + lb : -1;
-                            Kb[e] = bb >= 0 ? bb + la * sNstrB[eb[e] >> 23] + ((eb[e] >> 1) & DZ_LOC_MASK) : -1;
-                            sgn |= ((uint32_t)(ea[e] & 1) << e) | ((uint32_t)(eb[e] & 1) << (8 + e));
+                            const int32_t pat_b = max(eb[e] >> 23, 0);
+                            const int32_t ba = bA[max(ea[e] >> 23, 0) * npb];
+                            const int32_t bb = bB[pat_b];
+                            Ka[e] = (ea[e] >= 0 && ba >= 0) ? 2 * (ba + ((ea[e] >> 1) & DZ_LOC_MASK) * nb + lb) + (ea[e] & 1)
+                                                            : zero2;
+                            Kb[e] = (eb[e] >= 0 && bb >= 0) ? 2 * (bb + la * sNstrB[pat_b]) + (eb[e] & 0x7FFFFF) : zero2;
                         }
                     }
-                    int32_t xa[8], xb[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        xa[e] = __ldg(p.Cint + (Ka[e] < 0 ? 0 : Ka[e]));
-                        xb[e] = __ldg(p.Cint + (Kb[e] < 0 ? 0 : Kb[e]));
-                    }
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int32_t va = Ka[e] < 0 ? 0 : (((sgn >> e) & 1) ? -xa[e] : xa[e]);
-                        const int32_t vb = Kb[e] < 0 ? 0 : (((sgn >> (8 + e)) & 1) ? -xb[e] : xb[e]);
-                        y[u][e] = (uint32_t)(va + vb) + bias;
-                    }
+                    for (int e = 0; e < 8; ++e)
+                        y[u][e] = (uint32_t)(__ldg(p.Cint + Ka[e]) + __ldg(p.Cint + Kb[e])) + bias;
                 }
-                const int slot = (int)(q % (uint32_t)RING);
-                const uint32_t use = q / (uint32_t)RING;
-                if (use > 0 && !dz_wait_warp(smem_u32(&sh->plane_empty[slot]), (use - 1) & 1, abort, p.status,
-                                             p.timeout_cycles))
+                if (q >= (uint32_t)RING && !dz_wait_warp(smem_u32(&sh->plane_empty[slot]), ph ^ 1, abort, p.status,
+                                                         p.timeout_cycles))
                     goto producer_done;
                 {
                     uint8_t *sl = sRing + (size_t)slot * p.slot_bytes;
@@ -320,6 +316,10 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&sh->plane_full[slot]));
+                if (++slot == (uint32_t)RING) {
+                    slot = 0;
+                    ph ^= 1;
+                }
             }
         }
     producer_done:;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
         // ---------------------------------------------------------------- epilogue
         const int ew = warp - PW;
         const int qd = warp & 3;  // the TMEM lane quadrant this warp may access
-        (void)ew;
+        const int part = ew >> 2;  // the warps of a quadrant take its 16-column chunks in turn
         const int nck = Np / 16;
         const int row = 32 * qd + lane;  // determinant within the tile
         uint32_t tau = 0;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
             const uint32_t tl = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(buf * S * Np);
             float *Et = p.E + tile * ((int64_t)p.npair * DZ_TILE) + row;
 #pragma unroll 1
-            for (int ck = 0; ck < nck; ++ck) {
+            for (int ck = part; ck < nck; ck += EW / 4) {
                 int64_t acc[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) acc[c] = 0;
@@ -354,10 +354,16 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
                     for (int c = 0; c < 16; ++c)
                         acc[c] += (int64_t)__float2int_rn(__uint_as_float(vs[l][c])) * ((int64_t)1 << (8 * l));
                 }
+                // E = acc rounded to FP32 (|acc| < 2^40): acc = hi 2^16 + lo with |hi| < 2^24
+                // and 0 <= lo < 2^16 both exact in FP32, so one fused multiply-add rounds
+                // hi 2^16 + lo exactly as a direct int64 -> FP32 conversion would, with
+                // 32-bit conversions only
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const int pp = 16 * ck + c;
-                    if (pp < p.npair) __stcs(Et + (int64_t)pp * DZ_TILE, __ll2float_rn(acc[c]));
+                    const float hi = __int2float_rn((int32_t)(acc[c] >> 16));
+                    const float lo = __int2float_rn((int32_t)(acc[c] & 0xFFFF));
+                    if (pp < p.npair) __stcs(Et + (int64_t)pp * DZ_TILE, __fmaf_rn(hi, 65536.0f, lo));
                 }
             }
             tc_fence_before();
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
             bdesc[i] = smem_desc(smem_u32(sG) + (uint32_t)(i * p.g_slice_bytes), 128, (uint32_t)(KC * 128));
         const uint64_t adesc0 = smem_desc(smem_u32(sRing), 128, (uint32_t)(KCH * 128));
         const uint32_t slot_step = (uint32_t)(p.slot_bytes >> 4), plane_step = (uint32_t)(plane_bytes >> 4);
-        uint32_t q = 0, tau = 0;
+        uint32_t slot = 0, ph = 0, tau = 0;  // ring slot, its use parity, tile counter
         bool issued = false;
         for (int64_t tile = cta; tile < ntiles; tile += cta_n, ++tau) {
             const int buf = nbuf == 2 ? (int)(tau & 1) : 0;
@@ -384,10 +390,8 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
             tc_fence_after();
             const uint32_t dbase = tmem + (uint32_t)(buf * S * Np);
             bool ok = true;
-            for (int ch = 0; ch < nch; ++ch, ++q) {
-                const int slot = (int)(q % (uint32_t)RING);
-                if (!dz_wait(smem_u32(&sh->plane_full[slot]), (q / (uint32_t)RING) & 1, abort, p.status,
-                             p.timeout_cycles)) {
+            for (int ch = 0; ch < nch; ++ch) {
+                if (!dz_wait(smem_u32(&sh->plane_full[slot]), ph, abort, p.status, p.timeout_cycles)) {
                     ok = false;
                     break;
                 }
@@ -407,6 +411,10 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
                 }
                 issued = true;
                 mma_commit(smem_u32(&sh->plane_empty[slot]));
+                if (++slot == (uint32_t)RING) {
+                    slot = 0;
+                    ph ^= 1;
+                }
             }
             if (!ok) break;
             mma_commit(smem_u32(&sh->acc_full[buf]));
@@ -461,7 +469,9 @@ __global__ void k_dz_absmax(const double *__restrict__ x, int64_t n, unsigned lo
 }
 
 // C_int = round(C 2^{sh_C}), sh_C = 8 s - 3 - e_C with max|C| < 2^{e_C}: |C_int| < 2^{8s-3}
-// (< 2^21 for s <= 3, so int32 holds it).
+// (< 2^21 for s <= 3, so int32 holds it), stored as signed pairs (C_int, -C_int) per
+// determinant followed by one zero pair at index n: the producers read the value of a
+// move with its sign, or zero for an absent move, with one load and no arithmetic.
 __global__ void k_dz_to_fixed(const double *__restrict__ C, int64_t n, int s,
                               const unsigned long long *__restrict__ maxbits, int32_t *__restrict__ Cint,
                               int *__restrict__ shC) {
@@ -469,8 +479,11 @@ __global__ void k_dz_to_fixed(const double *__restrict__ C, int64_t n, int s,
     const int e = mb ? (int)((mb >> 52) & 0x7FF) - 1022 : 0;
     const int sh = 8 * s - 3 - e;
     if (blockIdx.x == 0 && threadIdx.x == 0) *shC = sh;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        Cint[i] = (int32_t)__double2ll_rn(scalbn(C[i], sh));
+    if (blockIdx.x == 0 && threadIdx.x == 0) *(int2 *)(Cint + 2 * n) = make_int2(0, 0);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = (int32_t)__double2ll_rn(scalbn(C[i], sh));
+        *(int2 *)(Cint + 2 * i) = make_int2(v, -v);
+    }
 }
 
 struct DzScatter {
@@ -809,8 +822,8 @@ int dz_prepare_job(fci_context *h, const double *C, double *sigma, int s, void *
     j.h = h;
     j.C = C;
     j.sigma = sigma;
-    j.Cint = (int32_t *)p;
-    p += al256((size_t)L.n_det * 4);
+    j.Cint = (int32_t *)p;  // signed pairs (+C, -C) per determinant, then a zero pair
+    p += al256((size_t)(L.n_det + 1) * 8);
     j.E = (float *)p;
     p += al256((size_t)ceil_div(max_len, DZ_TILE) * h->npair * DZ_TILE * 4);
     j.acc = nullptr;
@@ -953,7 +966,7 @@ size_t dz_workspace_bytes(const fci_context *h, int s) {
     std::vector<std::pair<int, int>> ch;
     int64_t max_len = 0;
     dz_chunks(h, ch, max_len);
-    size_t b = al256((size_t)h->das.n_det * 4) + al256((size_t)ceil_div(max_len, DZ_TILE) * h->npair * DZ_TILE * 4);
+    size_t b = al256((size_t)(h->das.n_det + 1) * 8) + al256((size_t)ceil_div(max_len, DZ_TILE) * h->npair * DZ_TILE * 4);
     if (ch.size() > 1) b += al256((size_t)h->das.n_det * 8);
     return b + 256;
 }
