@@ -28,11 +28,14 @@ def test_fci_tile_widths_agree(fci_lib, monkeypatch, n, na, nb, s):
         assert rel_inf(b.cpu().numpy(), oracle.sigma(p["hso"], p["gso"], p["dets"], c.cpu().numpy(), e_core=0.1)) <= SIGMA_RTOL
 
 
-@pytest.mark.parametrize("s", [2, 3, 6, 7])
-@pytest.mark.parametrize("n,na,nb", [(6, 3, 3), (9, 4, 3), (11, 6, 4), (13, 6, 6)])
+@pytest.mark.parametrize("s", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("n,na,nb", [(1, 1, 1), (5, 0, 3), (6, 3, 3), (9, 4, 3), (11, 6, 4), (13, 6, 6)])
 def test_fci_two_pass_path_agrees_with_fused(fci_lib, monkeypatch, n, na, nb, s):
     """The two-pass path (D digit image + bulk-copy GEMM) and the fused kernel compute the
-    same integers: identical bits, ragged N tiles and padded K chunks included."""
+    same integers: identical bits, ragged N tiles and padded K chunks included, for every
+    accumulator form (double-buffered s <= 4; one buffer released in two or three level
+    groups at s = 5..7) and for a single determinant and an empty alpha string set (one
+    tile, one K-chunk)."""
     p = fci_problem(n, na, nb, n_chol=n + 1, seed=90 + n, e_core=-0.2)
     f = gpu_fci(p)
     c = torch.from_numpy(synth.random_vector(len(p["dets"]), seed=6)).cuda()
