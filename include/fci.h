@@ -192,6 +192,14 @@ typedef struct {
                                vectors of the workspace (x copied in, y copied out by the
                                library), so a caller can replay a captured sigma graph for
                                the whole solve; default 0 */
+    double start_mix;       /* without a guess, the start vector is the unit vector at min
+                               H_II plus start_mix times a pseudo-random vector of norm ~1
+                               (splitmix64 of the index), normalised; default 1e-2.  The
+                               admixture reaches every symmetry sector, so the solve finds
+                               the lowest eigenvalue of H; 0 gives the bare unit vector,
+                               which for a closed-shell determinant of an M_s = 0 space is
+                               symmetric under alpha <-> beta exchange and converges to the
+                               lowest state of that sector only */
 } fci_davidson_opts;
 
 typedef struct {

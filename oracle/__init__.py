@@ -48,6 +48,12 @@ def lib() -> ctypes.CDLL:
         L.orc_dense_h.argtypes = [i32, vp, vp, i64, vp, vp]
         L.orc_sigma.argtypes = [i32, vp, vp, dbl, i64, vp, vp, vp, i64, vp]
         L.orc_sigma.restype = i32
+        L.orc_table_new.argtypes = [i64, vp]
+        L.orc_table_new.restype = vp
+        L.orc_table_free.argtypes = [vp]
+        L.orc_table_free.restype = None
+        L.orc_sigma_table.argtypes = [vp, i32, vp, vp, dbl, i64, vp, vp, vp, i64, vp]
+        L.orc_sigma_table.restype = i32
         L.orc_num_threads.restype = i32
         _LIB = L
     return _LIB
@@ -145,6 +151,44 @@ def sigma(hso, gso, dets, C, e_core: float = 0.0, rows=None):
         raise RuntimeError(f"orc_sigma failed ({rc})")
     real_in = (not np.iscomplexobj(C)) and np.all(np.imag(hso) == 0) and np.all(np.imag(gso) == 0)
     return out.real.copy() if real_in else out
+
+
+class SigmaTable:
+    """The determinant lookup table of one list, built once and reused by many sigma
+    calls over that list (the arithmetic is ``sigma``'s)."""
+
+    def __init__(self, dets):
+        self.dets = np.ascontiguousarray(dets, np.uint64)
+        self._t = lib().orc_table_new(len(self.dets), _ptr(self.dets))
+        if not self._t:
+            raise RuntimeError("orc_table_new failed (allocation or duplicate determinants)")
+
+    def close(self):
+        if getattr(self, "_t", None):
+            lib().orc_table_free(self._t)
+            self._t = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sigma(self, hso, gso, C, e_core: float = 0.0, rows=None):
+        nso = hso.shape[0]
+        h, g, c = _cplx(hso), _cplx(gso), _cplx(C)
+        if rows is None:
+            nrows, rp = len(self.dets), None
+        else:
+            rows = np.ascontiguousarray(rows, np.int64)
+            nrows, rp = len(rows), _ptr(rows)
+        out = np.empty(nrows, np.complex128)
+        rc = lib().orc_sigma_table(self._t, nso, _ptr(h), _ptr(g), float(e_core), len(self.dets), _ptr(self.dets),
+                                   _ptr(c), rp, nrows, _ptr(out))
+        if rc != 0:
+            raise RuntimeError(f"orc_sigma_table failed ({rc})")
+        real_in = (not np.iscomplexobj(C)) and np.all(np.imag(hso) == 0) and np.all(np.imag(gso) == 0)
+        return out.real.copy() if real_in else out
 
 
 def diag(hso, gso, dets):

@@ -282,15 +282,11 @@ int orc_dense_h(int nso, const double *h, const double *g, int64_t ndet, const u
  * in the order of `rows`.  C and sigma are interleaved complex.
  * J runs over I itself and all single and double replacements of I (every pair of
  * occupied spin orbitals replaced by every pair of empty ones) that are present in
- * the determinant list. */
-int orc_sigma(int nso, const double *h, const double *g, double e_core, int64_t ndet,
-              const uint64_t *dets, const double *Cin, const int64_t *rows, int64_t nrows,
-              double *sigma) {
+ * the determinant list, found through the lookup table `lut` of that list. */
+static int sigma_rows(const lut_t *lut, int nso, const double *h, const double *g, double e_core, int64_t ndet,
+                      const uint64_t *dets, const double *Cin, const int64_t *rows, int64_t nrows, double *sigma) {
     ham_t H = {nso, (const cplx *)h, (const cplx *)g};
     const cplx *C = (const cplx *)Cin;
-    lut_t lut;
-    int rc = lut_build(&lut, dets, ndet);
-    if (rc != 0) return rc;
     int bad = 0;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t r = 0; r < nrows; ++r) {
@@ -307,7 +303,7 @@ int orc_sigma(int nso, const double *h, const double *g, double e_core, int64_t 
         for (int a = 0; a < no; ++a) {
             for (int v = 0; v < nv; ++v) {
                 uint64_t J = (I & ~((uint64_t)1 << occ[a])) | ((uint64_t)1 << vir[v]);
-                int64_t j = lut_find(&lut, J);
+                int64_t j = lut_find(lut, J);
                 if (j < 0) continue;
                 acc = cadd(acc, cmul(h_elem(&H, I, J), C[j]));
             }
@@ -319,7 +315,7 @@ int orc_sigma(int nso, const double *h, const double *g, double e_core, int64_t 
                 for (int v = 0; v < nv; ++v) {
                     for (int w = v + 1; w < nv; ++w) {
                         uint64_t J = I2 | ((uint64_t)1 << vir[v]) | ((uint64_t)1 << vir[w]);
-                        int64_t j = lut_find(&lut, J);
+                        int64_t j = lut_find(lut, J);
                         if (j < 0) continue;
                         acc = cadd(acc, cmul(h_elem(&H, I, J), C[j]));
                     }
@@ -329,8 +325,43 @@ int orc_sigma(int nso, const double *h, const double *g, double e_core, int64_t 
         sigma[2 * r] = acc.re;
         sigma[2 * r + 1] = acc.im;
     }
-    lut_free(&lut);
     return bad ? -3 : 0;
+}
+
+/* sigma over a determinant list (see sigma_rows), with a lookup table built for this
+ * call. */
+int orc_sigma(int nso, const double *h, const double *g, double e_core, int64_t ndet,
+              const uint64_t *dets, const double *Cin, const int64_t *rows, int64_t nrows,
+              double *sigma) {
+    lut_t lut;
+    int rc = lut_build(&lut, dets, ndet);
+    if (rc != 0) return rc;
+    rc = sigma_rows(&lut, nso, h, g, e_core, ndet, dets, Cin, rows, nrows, sigma);
+    lut_free(&lut);
+    return rc;
+}
+
+/* The lookup table of a determinant list, built once for many orc_sigma_table calls on
+ * the same list (NULL on failure or duplicate determinants). */
+void *orc_table_new(int64_t ndet, const uint64_t *dets) {
+    lut_t *t = (lut_t *)malloc(sizeof(lut_t));
+    if (!t) return NULL;
+    if (lut_build(t, dets, ndet) != 0) { free(t); return NULL; }
+    return t;
+}
+
+void orc_table_free(void *t) {
+    if (!t) return;
+    lut_free((lut_t *)t);
+    free(t);
+}
+
+/* orc_sigma with a table from orc_table_new for the same determinant list. */
+int orc_sigma_table(const void *t, int nso, const double *h, const double *g, double e_core, int64_t ndet,
+                    const uint64_t *dets, const double *Cin, const int64_t *rows, int64_t nrows,
+                    double *sigma) {
+    if (!t) return -1;
+    return sigma_rows((const lut_t *)t, nso, h, g, e_core, ndet, dets, Cin, rows, nrows, sigma);
 }
 
 /* Number of threads OpenMP will use (for reporting the CPU baseline's core count). */

@@ -22,6 +22,8 @@
 // whose K lies in the chunk.
 #include <math.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <functional>
 #include <map>
@@ -326,13 +328,20 @@ int das_build(fci_context *h, int S, const int *orbs, const int *ref_a, const in
 
 // Chunk of the intermediate space processed per pass: whole categories, D and E both
 // resident; at most 16 GiB of workspace so very large spaces run in several passes.
+// FCI_DAS_FP64_CHUNK_DETS=n lowers the cap to n determinants (never below the largest
+// category), so that small problems can run the several-pass form too.
 static int64_t das_chunk_len(const fci_context *h) {
     const int64_t cap_bytes = (int64_t)16 << 30;
     const int64_t per_det = 2 * 8 * (int64_t)h->npair;
     const fci_das_layout &L = h->das;
     int64_t maxcat = 0;
     for (int c = 0; c < L.n_cat_int; ++c) maxcat = std::max(maxcat, L.cat_off[c + 1] - L.cat_off[c]);
-    return std::max(maxcat, std::min(L.n_det_int, cap_bytes / per_det));
+    int64_t cap = std::min(L.n_det_int, cap_bytes / per_det);
+    if (const char *env = getenv("FCI_DAS_FP64_CHUNK_DETS")) {
+        const long long v = atoll(env);
+        if (v > 0) cap = std::min<int64_t>(cap, v);
+    }
+    return std::max(maxcat, cap);
 }
 
 size_t das_workspace_bytes(const fci_context *h, int precision, int n_slices) {

@@ -371,10 +371,29 @@ __global__ void k_argmin(const double *__restrict__ d, int64_t n, int64_t *__res
     }
 }
 
-__global__ void k_set_unit(double *__restrict__ x, int64_t nreal, int cplx, const int64_t *__restrict__ idx) {
+// splitmix64 (Steele, Lea and Flood 2014, "Fast splittable pseudorandom number
+// generators"): the published finaliser of a 64-bit counter.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Start vector: the unit vector at idx plus, if mix > 0, mix times a pseudo-random vector
+// of norm about one (entries uniform in [-1, 1) from splitmix64 of the index, scaled by
+// sqrt(3 / nreal)).  The admixture gives the start a component in every symmetry sector
+// (a closed-shell unit vector alone is symmetric under alpha <-> beta exchange, and the
+// iteration would stay in that sector).
+__global__ void k_set_start(double *__restrict__ x, int64_t nreal, int cplx, const int64_t *__restrict__ idx,
+                            double mix) {
     const int64_t at = (cplx ? 2 : 1) * (*idx);
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nreal; j += (int64_t)gridDim.x * blockDim.x)
-        x[j] = (j == at) ? 1.0 : 0.0;
+    const double scale = mix * sqrt(3.0 / (double)nreal);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nreal; j += (int64_t)gridDim.x * blockDim.x) {
+        double v = (j == at) ? 1.0 : 0.0;
+        if (mix > 0.0) v += scale * (2.0 * (double)(splitmix64((uint64_t)j) >> 11) * 0x1.0p-53 - 1.0);
+        x[j] = v;
+    }
 }
 
 inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -510,7 +529,7 @@ struct fci_davidson_state {
             FCI_CUDA(h, cudaMemcpyAsync(Vk(0), guess, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
         } else {
             k_argmin<<<1, 256, 0, s>>>(diag, n, argmin);
-            k_set_unit<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, cplx, argmin);
+            k_set_start<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, cplx, argmin, o.start_mix);
         }
         FCI_CUDA(h, normalize(Vk(0), nrm));
         return ask(REQ_INIT, Vk(0), Sk(0));

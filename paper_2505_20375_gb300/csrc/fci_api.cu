@@ -35,12 +35,25 @@ int fci_cuda_check(fci_context *h, cudaError_t e, const char *what) {
 }
 
 // Device allocation with host-side fault injection: FCI_FAULT_ALLOC_AT=n makes the n-th
-// allocation of the process (counting from 1) fail as if the device were out of memory.
+// allocation (counting from 1) fail as if the device were out of memory, counting from
+// the first allocation that sees the variable with its current value (setting it anew, or
+// unsetting it, restarts the count).
 int fci_dev_alloc(fci_context *h, void **p, size_t bytes) {
     *p = nullptr;
-    long k = ++g_alloc_count;
-    const char *inj = getenv("FCI_FAULT_ALLOC_AT");
-    if (inj && atol(inj) == k) return fci_fail(h, FCI_ERR_OOM, "injected allocation failure #%ld", k);
+    {
+        static std::mutex mu;
+        static std::string seen;
+        static long base = 0;
+        std::lock_guard<std::mutex> lk(mu);
+        const long k = ++g_alloc_count;
+        const char *inj = getenv("FCI_FAULT_ALLOC_AT");
+        const std::string now = inj ? inj : "";
+        if (now != seen) {
+            seen = now;
+            base = k - 1;
+        }
+        if (inj && atol(inj) == k - base) return fci_fail(h, FCI_ERR_OOM, "injected allocation failure #%ld", k - base);
+    }
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
@@ -211,10 +224,13 @@ int fci_create(fci_handle *out, int device) {
     if (!rc) rc = fci_cuda_check(h, cudaMemcpy(h->d_binom, bt.data(), bt.size() * 8, cudaMemcpyHostToDevice), "binom upload");
     h->small_bytes = 1 << 20;
     if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_small, h->small_bytes);
+    if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_status, 256);
+    if (!rc) rc = fci_cuda_check(h, cudaMemset(h->d_status, 0, 256), "status word");
     if (rc) {
         g_err = h->err;
         fci_dev_free(h->d_binom);
         fci_dev_free(h->d_small);
+        fci_dev_free(h->d_status);
         delete h;
         return rc;
     }
@@ -247,10 +263,9 @@ int fci_sync_status(fci_handle h, fci_stream stream) {
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     FCI_CUDA(h, cudaStreamSynchronize(s));
-    if (!h->last_status) return FCI_OK;
     int st = 0;
-    FCI_CUDA(h, cudaMemcpy(&st, h->last_status, sizeof st, cudaMemcpyDeviceToHost));
-    FCI_CUDA(h, cudaMemset(h->last_status, 0, sizeof st));
+    FCI_CUDA(h, cudaMemcpy(&st, h->d_status, sizeof st, cudaMemcpyDeviceToHost));
+    FCI_CUDA(h, cudaMemset(h->d_status, 0, sizeof st));
     if (st == FCI_ERR_TIMEOUT) return fci_fail(h, FCI_ERR_TIMEOUT, "a bounded device wait expired; sigma was set to NaN");
     if (st) return fci_fail(h, st, "device status %d", st);
     return FCI_OK;
@@ -265,6 +280,7 @@ int fci_destroy(fci_handle h) {
     free_strings(h);
     fci_dev_free(h->d_binom);
     fci_dev_free(h->d_small);
+    fci_dev_free(h->d_status);
     delete h;
     return FCI_OK;
 }
@@ -541,6 +557,7 @@ void fci_davidson_default_opts(fci_davidson_opts *o) {
     o->final_slices = 0;
     o->staged_sigma = 0;
     o->gap_bound = 0;
+    o->start_mix = 1e-2;
 }
 
 static int check_opts(fci_context *h, const fci_davidson_opts *o) {
@@ -549,6 +566,8 @@ static int check_opts(fci_context *h, const fci_davidson_opts *o) {
         return fci_fail(h, FCI_ERR_ARG, "max_iter >= 1 and max_subspace in [2, 32] required");
     if (!(o->tol_residual > 0) || !(o->tol_energy > 0) || !(o->eps == o->eps))
         return fci_fail(h, FCI_ERR_ARG, "tolerances must be positive, eps a number");
+    if (!(o->start_mix >= 0.0 && o->start_mix <= 1.0))
+        return fci_fail(h, FCI_ERR_ARG, "start_mix must lie in [0, 1]");
     if (o->precision != FCI_PREC_FP64 && o->precision != FCI_PREC_OZ_BF16)
         return fci_fail(h, FCI_ERR_ARG, "unknown precision %d", o->precision);
     if (o->precision == FCI_PREC_OZ_BF16 && (o->n_slices < 2 || o->n_slices > 8))
@@ -677,10 +696,13 @@ int fci_tune_sigma(fci_handle h, int n_slices, const void *C, void *sigma, void 
         for (int r = 0; r < reps && !rc; ++r) rc = sigma_dispatch(h, C, sigma, FCI_PREC_OZ_BF16, n_slices, ws, ws_bytes, s);
         if (!rc) rc = fci_cuda_check(h, cudaEventRecord(e1, s), "event");
         if (!rc) rc = fci_cuda_check(h, cudaEventSynchronize(e1), "sync");
-        if (!rc && h->last_status) {
+        if (!rc) {
             int st = 0;
-            rc = fci_cuda_check(h, cudaMemcpy(&st, h->last_status, sizeof(int), cudaMemcpyDeviceToHost), "status");
-            if (!rc && st) rc = fci_fail(h, st, "split-precision kernel reported status %d while tuning", st);
+            rc = fci_cuda_check(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost), "status");
+            if (!rc && st) {
+                cudaMemset(h->d_status, 0, sizeof(int));
+                rc = fci_fail(h, st, "split-precision kernel reported status %d while tuning", st);
+            }
         }
         float t = 0.f;
         if (!rc) rc = fci_cuda_check(h, cudaEventElapsedTime(&t, e0, e1), "elapsed");

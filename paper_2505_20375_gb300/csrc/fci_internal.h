@@ -130,8 +130,10 @@ struct fci_context {
     };
     std::vector<graph_rec> graphs;
 
-    // device status word of the last split-precision sigma (inside the caller's workspace)
-    int *last_status = nullptr;
+    // device status word owned by the handle: a split-precision sigma whose bounded wait
+    // expired records FCI_ERR_TIMEOUT here (through its scatter kernel); it stays set until
+    // fci_sync_status reads and clears it, whatever happens to the caller's workspace
+    int *d_status = nullptr;
 
     // scratch for reductions (small)
     double *d_small = nullptr;

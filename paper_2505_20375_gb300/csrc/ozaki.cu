@@ -380,13 +380,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_oz_contract(const __grid_cons
             mma_commit(smem_u32(&sh->acc_full[buf]));
         }
         if (issued) {  // drain: every MMA this thread issued has completed before TMEM is freed
+            // every MMA issued must complete before TMEM is freed: a first bounded wait,
+            // and a second one if the first expires (FCI_ERR_TIMEOUT recorded)
             mma_commit(smem_u32(&sh->drain));
-            const long long t0 = clock64();
-            while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
-                if (clock64() - t0 > p.timeout_cycles) {
-                    atomicExch(p.status, FCI_ERR_TIMEOUT);
-                    break;
+            for (int pass = 0; pass < 2; ++pass) {
+                const long long t0 = clock64();
+                bool done = true;
+                while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
+                    if (clock64() - t0 > p.timeout_cycles) {
+                        atomicExch(p.status, FCI_ERR_TIMEOUT);
+                        done = false;
+                        break;
+                    }
                 }
+                if (done) break;
             }
         }
     }
@@ -430,11 +437,12 @@ __global__ void __launch_bounds__(256) k_scatter_int(uint32_t nsa, uint32_t nsb,
                                                      const int64_t *__restrict__ E, int64_t ldE,
                                                      const double *__restrict__ C, double e_core, int ushift,
                                                      const int *__restrict__ shC, const int *__restrict__ status,
-                                                     double *__restrict__ sigma) {
+                                                     int *__restrict__ sticky, double *__restrict__ sigma) {
     const uint32_t ib = blockIdx.x * blockDim.x + threadIdx.x;
     if (ib >= nsb) return;
     const int u = ushift - *shC;
     const bool bad = *status != 0;
+    if (bad && ib == 0 && blockIdx.y == 0) atomicExch(sticky, *status);  // kept for fci_sync_status
     // E is tile-major: element (pq, K) at (K / T) * R * T + pq * T + K % T, T = 2^log2T,
     // R = ldE rows per tile (n_pair for the fused kernel, 128 for the two-pass GEMM).
     // Determinant indices are 32-bit (ndet < 2^31); a pair-table entry e is 2 x (source
@@ -712,7 +720,6 @@ static int oz_prepare_job(fci_context *h, const double *C, int s, void *ws, cuda
     unsigned long long *maxbits = (unsigned long long *)p;
     int *shC = (int *)(p + 8);
     int *status = (int *)(p + 16);
-    h->last_status = status;
     {
         phase_scope ps(h, st, FCI_PHASE_OTHER, 2);
         FCI_CUDA(h, cudaMemsetAsync(p, 0, 256, st));
@@ -780,7 +787,7 @@ static int oz_finish_job(fci_context *h, const double *C, double *sigma, const O
     k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair_pad, prm.nt == 32 ? 5 : 6, h->d_pair_a, h->d_pair_b,
                                        E, prm.npair,
                                        C, h->e_core,
-                                       8 * prm.L0 - h->G_exp, shC, status, sigma);
+                                       8 * prm.L0 - h->G_exp, shC, status, h->d_status, sigma);
     FCI_CUDA(h, cudaGetLastError());
     return FCI_OK;
 }
@@ -813,7 +820,6 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
     char *misc = (char *)ws + (oz_workspace_bytes(h, s) - 256);
     unsigned long long *maxbits = (unsigned long long *)misc;
     int *shC = (int *)(misc + 8), *status = (int *)(misc + 16);
-    h->last_status = status;
     {
         phase_scope ps(h, st, FCI_PHASE_GATHER, 3);
         FCI_CUDA(h, cudaMemsetAsync(misc, 0, 256, st));
@@ -849,7 +855,7 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
     const int threads = 128;
     dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
     k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair_pad, 6, h->d_pair_a, h->d_pair_b, E, OZG_M, C,
-                                       h->e_core, 8 * oz_gemm_L0(s, 8) - h->G_exp, shC, status, sigma);
+                                       h->e_core, 8 * oz_gemm_L0(s, 8) - h->G_exp, shC, status, h->d_status, sigma);
     FCI_CUDA(h, cudaGetLastError());
     return FCI_OK;
 }

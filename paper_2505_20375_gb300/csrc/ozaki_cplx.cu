@@ -150,11 +150,13 @@ __global__ void __launch_bounds__(128) k_cz_scatter(int n, int64_t ndet, int M_p
                                                     const uint64_t *__restrict__ binom,
                                                     const int64_t *__restrict__ E, const double *__restrict__ C,
                                                     double e_core, int ushift, const int *__restrict__ shC,
-                                                    const int *__restrict__ status, double *__restrict__ sigma) {
+                                                    const int *__restrict__ status, int *__restrict__ sticky,
+                                                    double *__restrict__ sigma) {
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (I >= ndet) return;
     const int u = ushift - *shC;
     const bool bad = *status != 0;
+    if (bad && I == 0) atomicExch(sticky, *status);  // kept for fci_sync_status
     const uint32_t Sm = (uint32_t)str[I];
     int64_t ar = 0, ai = 0;
     for (int a = 0; a < n; ++a) {
@@ -288,7 +290,6 @@ int cz_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, si
     p += al256((size_t)g.n_nt * g.M_pad * CZ_N * 8);
     unsigned long long *maxbits = (unsigned long long *)p;
     int *shC = (int *)(p + 8), *status = (int *)(p + 16);
-    h->last_status = status;
     {
         phase_scope ps(h, st, FCI_PHASE_GATHER, 3);
         FCI_CUDA(h, cudaMemsetAsync(p, 0, 256, st));
@@ -322,7 +323,8 @@ int cz_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, si
         const int L0 = oz_gemm_L0(s, 7);
         k_cz_scatter<<<(unsigned)ceil_div(h->ndet, 128), 128, 0, st>>>(h->n_orb, h->ndet, g.M_pad, h->d_str_a,
                                                                         h->d_binom, E, C, h->e_core,
-                                                                        7 * L0 - h->G_exp, shC, status, sigma);
+                                                                        7 * L0 - h->G_exp, shC, status, h->d_status,
+                                                                        sigma);
         FCI_CUDA(h, cudaGetLastError());
     }
     return FCI_OK;

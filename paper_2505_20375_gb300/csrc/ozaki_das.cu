@@ -82,6 +82,7 @@ struct DzParams {
     float *E;
     int *status;
     long long timeout_cycles;
+    int stall_test;  // test hook: producers never signal a filled slot, so the MMA wait expires
 };
 
 struct DzGroup {
@@ -315,7 +316,7 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&sh->plane_full[slot]));
+                if (lane == 0 && !p.stall_test) mbar_arrive(smem_u32(&sh->plane_full[slot]));
                 if (++slot == (uint32_t)RING) {
                     slot = 0;
                     ph ^= 1;
@@ -420,13 +421,20 @@ __global__ void __launch_bounds__(dz_threads(PW), 1) k_oz_das(const __grid_const
             mma_commit(smem_u32(&sh->acc_full[buf]));
         }
         if (issued) {
+            // every MMA issued must complete before TMEM is freed: a first bounded wait,
+            // and a second one if the first expires (FCI_ERR_TIMEOUT recorded)
             mma_commit(smem_u32(&sh->drain));
-            const long long t0 = clock64();
-            while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
-                if (clock64() - t0 > p.timeout_cycles) {
-                    atomicExch(p.status, FCI_ERR_TIMEOUT);
-                    break;
+            for (int pass = 0; pass < 2; ++pass) {
+                const long long t0 = clock64();
+                bool done = true;
+                while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
+                    if (clock64() - t0 > p.timeout_cycles) {
+                        atomicExch(p.status, FCI_ERR_TIMEOUT);
+                        done = false;
+                        break;
+                    }
                 }
+                if (done) break;
             }
         }
     }
@@ -500,6 +508,7 @@ struct DzScatter {
     double e_core;
     int ushift;  // 8 (s - 1) - sh_G; the scale is 2^(ushift - sh_C)
     const int *shC, *status;
+    int *sticky;  // the handle's status word (fci_sync_status)
     int mode;    // 0: single chunk (write sigma); 1: first of several; 2: middle; 3: last
     int64_t *acc;
     double *sigma;
@@ -521,6 +530,7 @@ __global__ void __launch_bounds__(256) k_dz_scatter(const __grid_constant__ DzSc
     int32_t *row = rowAll + (threadIdx.x >> 5) * npb;
     const int u = a.ushift - *a.shC;
     const bool bad = *a.status != 0;
+    if (bad && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.sticky, *a.status);  // kept for fci_sync_status
     const int64_t tstride = (int64_t)a.npair * DZ_TILE;
     const int32_t len = (int32_t)a.len, a0 = (int32_t)a.a0;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -834,7 +844,6 @@ int dz_prepare_job(fci_context *h, const double *C, double *sigma, int s, void *
     unsigned long long *maxbits = (unsigned long long *)p;
     j.shC = (int *)(p + 8);
     j.status = (int *)(p + 16);
-    h->last_status = j.status;
     phase_scope ps(h, st, FCI_PHASE_OTHER, 2);
     FCI_CUDA(h, cudaMemsetAsync(p, 0, 256, st));
     const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(L.n_det, 256), 152 * 8);
@@ -879,6 +888,8 @@ void dz_params(const DzJob &j, int s, const DzGeom &g, int chunk, DzParams &prm)
     const char *to = getenv("FCI_WAIT_TIMEOUT_MS");
     const double ms = to ? atof(to) : 2000.0;
     prm.timeout_cycles = (long long)(ms * 2.1e6);
+    const char *stall = getenv("FCI_TEST_STALL_PRODUCER");
+    prm.stall_test = stall ? atoi(stall) : 0;
     (void)s;
 }
 
@@ -931,6 +942,7 @@ int dz_scatter(const DzJob &j, int s, int chunk, cudaStream_t st) {
     a.ushift = 8 * (s - 1) - L.dz_shG;
     a.shC = j.shC;
     a.status = j.status;
+    a.sticky = h->d_status;
     a.mode = nchunks == 1 ? 0 : chunk == 0 ? 1 : chunk == nchunks - 1 ? 3 : 2;
     a.acc = j.acc;
     a.sigma = j.sigma;

@@ -12,8 +12,9 @@
 // released it.  Work units
 // are (N-tile, M-tile) pairs, N-tile outer and dealt round-robin, so the M-tiles of one
 // B tile run at about the same time and its reads hit L2.  Every mbarrier wait is bounded
-// in time (FCI_ERR_TIMEOUT in the status word on expiry; the kernel drains the MMAs it
-// issued and frees TMEM before returning).
+// in time (FCI_ERR_TIMEOUT in the status word on expiry; the kernel then waits, under a
+// bound of its own, for the bulk copies and MMAs it issued, and frees TMEM before
+// returning).
 #include <stdlib.h>
 
 #include <algorithm>
@@ -50,6 +51,7 @@ struct OzgParams {
     int64_t *E;
     int *status;
     long long timeout_cycles;
+    int stall_test;  // test hook: the MMA thread issues nothing, so the producer's wait expires
 };
 
 struct OzgShared {
@@ -74,6 +76,19 @@ __device__ __forceinline__ bool ozg_wait(uint32_t bar, uint32_t parity, volatile
                 atomicExch(status, FCI_ERR_TIMEOUT);
                 return false;
             }
+        }
+    }
+    return true;
+}
+
+// Wait for a phase that must complete (copies or MMAs already issued) before the CTA may
+// leave: bounded like every other wait, but blind to the abort flag.
+__device__ __forceinline__ bool ozg_drain_wait(uint32_t bar, uint32_t parity, int *status, long long timeout) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > timeout) {
+            atomicExch(status, FCI_ERR_TIMEOUT);
+            return false;
         }
     }
     return true;
@@ -165,6 +180,16 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
                 }
                 if (!ok) break;
             }
+            // Every copy issued must land before the CTA leaves, also after an abort (the
+            // copies of the stages the MMA thread never consumed are still in flight): wait
+            // for the last use of each ring slot, and for the resident A image.
+            const uint32_t used = q < (uint32_t)R ? q : (uint32_t)R;
+            for (uint32_t k = 1; k <= used; ++k) {
+                const uint32_t idx = q - k;
+                ozg_drain_wait(smem_u32(&sh->full[idx % (uint32_t)R]), (idx / (uint32_t)R) & 1u, p.status,
+                               p.timeout_cycles);
+            }
+            if (RESA) ozg_drain_wait(smem_u32(&sh->a_full), 0, p.status, p.timeout_cycles);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -178,8 +203,8 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
             const uint64_t a0 = smem_desc(smem_u32(sA), 128, KCC * 128);
             const uint64_t b0 = smem_desc(smem_u32(sB), 128, KCC * 128);
             uint32_t st = 0, ph = 0, tau = 0;  // ring slot, its use parity, unit counter
-            bool issued = false, ok = true;
-            if (RESA && !wait(smem_u32(&sh->a_full), 0)) ok = false;
+            bool issued = false, ok = !p.stall_test;
+            if (ok && RESA && !wait(smem_u32(&sh->a_full), 0)) ok = false;
             for (int64_t u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++tau) {
                 const int buf = NBUF == 2 ? (int)(tau & 1) : 0;
                 if (NBUF == 2 && tau >= 2) {
@@ -242,14 +267,12 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
                 mma_commit(smem_u32(&sh->acc_full[buf]));
             }
             if (issued) {
+                // all MMAs issued must complete before TMEM is freed; if the first budget
+                // expires (FCI_ERR_TIMEOUT recorded) a second one follows before the
+                // deallocation goes ahead
                 mma_commit(smem_u32(&sh->drain));
-                const long long t0 = clock64();
-                while (!mbar_try_wait(smem_u32(&sh->drain), 0)) {
-                    if (clock64() - t0 > p.timeout_cycles) {
-                        atomicExch(p.status, FCI_ERR_TIMEOUT);
-                        break;
-                    }
-                }
+                if (!ozg_drain_wait(smem_u32(&sh->drain), 0, p.status, p.timeout_cycles))
+                    ozg_drain_wait(smem_u32(&sh->drain), 0, p.status, p.timeout_cycles);
             }
         }
     } else {
@@ -404,6 +427,8 @@ int oz_gemm_launch(fci_context *h, int s, int w, int kcc, bool resa, const oz_ge
     prm.status = a.status;
     const char *to = getenv("FCI_WAIT_TIMEOUT_MS");
     prm.timeout_cycles = (long long)((to ? atof(to) : 2000.0) * 2.1e6);
+    const char *stall = getenv("FCI_TEST_STALL_PRODUCER");
+    prm.stall_test = stall ? atoi(stall) : 0;
     int nsm = 0;
     FCI_CUDA(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device));
     const size_t a_plane = (size_t)OZG_M * kcc * 16, b_plane = (size_t)OZG_N * kcc * 16;

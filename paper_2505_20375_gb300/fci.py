@@ -47,7 +47,7 @@ class fci_davidson_opts(ctypes.Structure):
     _fields_ = [("max_iter", _i32), ("max_subspace", _i32), ("tol_residual", _dbl), ("tol_energy", _dbl),
                 ("eps", _dbl), ("precision", _i32), ("n_slices", _i32), ("switch_residual", _dbl),
                 ("use_guess", _i32), ("final_precision", _i32), ("final_slices", _i32), ("gap_bound", _i32),
-                ("staged_sigma", _i32)]
+                ("staged_sigma", _i32), ("start_mix", _dbl)]
 
 
 class fci_davidson_iter(ctypes.Structure):
@@ -301,9 +301,11 @@ class FCI:
 
     def davidson_opts(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                       precision="fp64", n_slices=6, switch_residual=1e-5, final_precision="fp64", final_slices=0,
-                      use_guess=False, staged_sigma=False, gap_bound=False) -> fci_davidson_opts:
+                      use_guess=False, staged_sigma=False, gap_bound=False, start_mix=None) -> fci_davidson_opts:
         o = fci_davidson_opts()
         _dav_defaults(ctypes.byref(o))
+        if start_mix is not None:
+            o.start_mix = start_mix
         o.max_iter, o.max_subspace = max_iter, max_subspace
         o.tol_residual, o.tol_energy, o.eps = tol_residual, tol_energy, eps
         o.precision, o.n_slices, o.switch_residual = PRECISIONS[precision], n_slices, switch_residual
@@ -320,9 +322,12 @@ class FCI:
 
     def davidson(self, max_iter=100, max_subspace=32, tol_residual=1e-6, tol_energy=1e-10, eps=0.0,
                  precision="fp64", n_slices=6, switch_residual=1e-5, guess: torch.Tensor = None,
-                 final_precision="fp64", final_slices=0, gap_bound=False, stream=None) -> DavidsonResult:
+                 final_precision="fp64", final_slices=0, gap_bound=False, start_mix=None,
+                 stream=None) -> DavidsonResult:
         o = fci_davidson_opts()
         _dav_defaults(ctypes.byref(o))
+        if start_mix is not None:
+            o.start_mix = start_mix
         o.max_iter, o.max_subspace = max_iter, max_subspace
         o.tol_residual, o.tol_energy, o.eps = tol_residual, tol_energy, eps
         o.precision, o.n_slices, o.switch_residual = PRECISIONS[precision], n_slices, switch_residual

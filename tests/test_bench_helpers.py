@@ -1,6 +1,9 @@
-"""CPU tests of bench.py's host logic: the DRAM-traffic record is reported only for the
-kernel sources it was measured on."""
+"""CPU tests of bench.py's host logic: the roofline follows the method's work, and the
+DRAM-traffic record is reported only for the kernel sources it was measured on."""
+import json
 import os
+
+import pytest
 
 import bench
 
@@ -14,20 +17,24 @@ def _fake_tree(tmp_path, gemm_src=b"kernel v1"):
     return tmp_path
 
 
+def _write(root, recs):
+    (root / "profiles" / "traffic.json").write_text(json.dumps({"records": recs}))
+
+
 def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
     root = _fake_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
     sha = bench._kernel_sources_sha("k_oz_gemm<6,8>")
     assert len(sha) == 16
-    (root / "profiles" / "traffic.md").write_text(
-        "| kernel | workload | sources sha | dram bytes per launch | read | write |\n"
-        "|---|---|---|---|---|---|\n"
-        f"| k_oz_gemm<6,8> | fci_14e14o | {sha} | 25726923008 | 15.88 GB | 9.85 GB |\n"
-        f"| k_oz_gemm<6,8> | fci_12e12o | {sha} | 1308891904 | 0.82 GB | 0.49 GB |\n")
-    assert bench._traffic_record("k_oz_gemm<6,8>", "fci_14e14o") == 25726923008.0
-    assert bench._traffic_record("k_oz_gemm<6,8>", "fci_12e12o") == 1308891904.0
-    assert bench._traffic_record("k_oz_gemm<6,8>", "fci_8e8o") is None  # no row for the workload
-    assert bench._traffic_record("k_oz_gemm<7,8>", "fci_14e14o") is None  # no row for the form
+    _write(root, [{"kernel": "k_oz_gemm<6,8>", "workload": "fci_14e14o", "sources_sha": sha,
+                   "dram_bytes_per_launch": 25726923008, "date": "2026-12-03", "scaled_from": "fci_12e12o"},
+                  {"kernel": "k_oz_gemm<6,8>", "workload": "fci_12e12o", "sources_sha": sha,
+                   "dram_bytes_per_launch": 1308891904}])
+    r = bench._traffic_record("k_oz_gemm<6,8>", "fci_14e14o")
+    assert r["bytes"] == 25726923008.0 and r["scaled_from"] == "fci_12e12o" and r["sources_sha"] == sha
+    assert bench._traffic_record("k_oz_gemm<6,8>", "fci_12e12o")["bytes"] == 1308891904.0
+    assert bench._traffic_record("k_oz_gemm<6,8>", "fci_8e8o") is None  # no record for the workload
+    assert bench._traffic_record("k_oz_gemm<7,8>", "fci_14e14o") is None  # no record for the form
 
     # a changed kernel source invalidates the record: the bench reports null, not a stale count
     (root / "paper_2505_20375_gb300" / "csrc" / "ozaki_gemm.cu").write_bytes(b"kernel v2")
@@ -40,7 +47,28 @@ def test_traffic_record_follows_the_kernel_sources(tmp_path, monkeypatch):
 def test_traffic_record_without_a_capture(tmp_path, monkeypatch):
     root = _fake_tree(tmp_path)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    assert not os.path.exists(root / "profiles" / "traffic.md")
+    assert not os.path.exists(root / "profiles" / "traffic.json")
     assert bench._traffic_record("k_oz_gemm<6,8>", "fci_14e14o") is None
-    (root / "profiles" / "traffic.md").write_text("| k_oz_gemm<6,8> | fci_14e14o | 0123456789abcdef | n/a |\n")
+    _write(root, [{"kernel": "k_oz_gemm<6,8>", "workload": "fci_14e14o", "sources_sha": "0123456789abcdef",
+                   "dram_bytes_per_launch": 1}])
     assert bench._traffic_record("k_oz_gemm<6,8>", "fci_14e14o") is None
+    (root / "profiles" / "traffic.json").write_text("not json")
+    assert bench._traffic_record("k_oz_gemm<6,8>", "fci_14e14o") is None
+
+
+def test_split_roofline_counts_the_methods_packed_work():
+    """FCI(14e,14o), s = 6: 2 x 105^2 x 21 flop per determinant over 11,778,624
+    determinants = 5.45e12 flop per launch; at 7.857 ms that is 694 TF/s, 0.359 of a
+    1,933.5 TF/s peak.  The executed MMA shape (128 x 112, 64-determinant tiles) is 1.30x
+    more and is reported apart; the whole step is compared with the 2.82 ms the work needs
+    at the peak."""
+    r = bench.split_roofline(105, 11778624, 6, 7.857, 14.65, 1933.5, two_pass=True)
+    assert r["flops_per_launch"] == pytest.approx(2 * 105 ** 2 * 21 * 11778624)
+    assert r["flops_per_launch"] == pytest.approx(5.4543e12, rel=1e-4)
+    assert r["achieved"] == pytest.approx(694.2, rel=1e-3)
+    assert r["frac"] == pytest.approx(0.359, abs=1e-3)
+    ex = r["executed"]["flops_per_launch"] / r["flops_per_launch"]
+    assert ex == pytest.approx(128 * 112 * (-(-11778624 // 64) * 64) / (105 * 105 * 11778624))
+    assert 1.29 < ex < 1.31
+    assert r["step"]["tensor_floor_ms"] == pytest.approx(5.4543e12 / 1933.5e12 * 1e3, rel=1e-4)
+    assert r["step"]["frac"] == pytest.approx(r["step"]["tensor_floor_ms"] / 14.65)

@@ -119,3 +119,77 @@ def test_das_davidson_matches_dense_eigh(fci_lib):
     r = f.davidson(tol_residual=1e-6, tol_energy=1e-10)
     assert r.converged
     assert abs(r.energy - (np.linalg.eigvalsh(H)[0] - 1.0)) < ENERGY_TOL
+
+
+def test_das_fp64_several_chunks_matches_oracle(fci_lib, monkeypatch):
+    """The FP64 DAS sigma in several passes over the intermediate space (each pass adds
+    its part of sigma): capped at a quarter of the intermediate determinants it takes at
+    least three passes, and matches the oracle as the single pass does."""
+    spaces, ref, nel, T = [3, 3, 2], [1, 2, 1], 4, 1
+    p, f = das_problem(spaces, ref, nel, T, n_chol=9, seed=37, e_core=0.3)
+    dets, cats = odas.das_dets(spaces, ref, ref, nel, nel, T)
+    hso, gso = oracle.spin_orbital_integrals(p["h"], p["g"])
+    c = synth.random_vector(len(dets), seed=7)
+    refv = oracle.sigma(hso, gso, dets, c, e_core=0.3)
+    cd = torch.from_numpy(c).cuda()
+    one = f.sigma(cd).cpu().numpy()
+    n_int = f.info["n_det_intermediate"]
+    largest = max(na * nb for _, _, na, nb, _ in cats)
+    cap = max(n_int // 4, largest)
+    monkeypatch.setenv("FCI_DAS_FP64_CHUNK_DETS", str(cap))
+    f.set_phase_timing(True)
+    f.phase_times(reset=True)
+    many = f.sigma(cd).cpu().numpy()
+    passes = f.phase_times(reset=True)["contract"]["launches"]
+    f.set_phase_timing(False)
+    assert passes >= 3
+    assert rel_inf(many, refv) <= SIGMA_RTOL
+    assert rel_inf(one, refv) <= SIGMA_RTOL
+    assert rel_inf(many, one) <= 1e-13
+
+
+@pytest.fixture(scope="module")
+def das_16e():
+    """16 orbitals in 4 spaces of 4, 8 alpha + 8 beta electrons, <= 2 transfers: 253
+    categories, 78,444,288 determinants (138,495,744 in the intermediate space)."""
+    import oracle as _or
+
+    w = synth.WORKLOADS["das_16o_4x4"]
+    h, g = synth.real_integrals(w["n"], w["n_chol"], w["seed"])
+    from paper_2505_20375_gb300 import fci
+
+    f = fci.FCI(0).setup_integrals(h, g).build_strings(8, 8).build_das(w["spaces"], w["ref"], w["ref"],
+                                                                        w["max_transfer"])
+    dets, _ = odas.das_dets(w["spaces"], w["ref"], w["ref"], 8, 8, w["max_transfer"])
+    hso, gso = _or.spin_orbital_integrals(h, g)
+    c = synth.random_vector(len(dets), seed=7)
+    st = synth.Stream(19)
+    rows = np.concatenate([np.unique((st.uniform(120) * len(dets)).astype(np.int64)), [0, len(dets) - 1]])
+    ref = _or.sigma(hso, gso, dets, c, rows=rows)
+    del dets
+    s64 = f.sigma(torch.from_numpy(c).cuda()).cpu().numpy()
+    yield f, c, rows, ref, s64
+    f.close()
+    torch.cuda.empty_cache()
+
+
+def test_das_16e_fp64_sampled_rows(fci_lib, das_16e):
+    """The FP64 DAS sigma at 78 M determinants (several passes over the 138 M intermediate
+    determinants, each pass within 16 GiB of D and E) on sampled rows the oracle computes."""
+    f, c, rows, ref, s64 = das_16e
+    assert f.n_det == 78444288
+    assert np.max(np.abs(s64[rows] - ref)) / np.max(np.abs(s64)) <= SIGMA_RTOL
+
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_das_16e_split_sampled_rows(fci_lib, das_16e, s):
+    """The split-precision DAS sigma at 78 M determinants, in the launch configuration the
+    benchmark times, on the same sampled rows: within the per-slice tolerance."""
+    from test_split_model import DZ_TOL
+
+    f, c, rows, ref, s64 = das_16e
+    sg = f.sigma(torch.from_numpy(c).cuda(), precision="oz_bf16", n_slices=s).cpu().numpy()
+    f.sync_status()
+    scale = np.max(np.abs(s64))
+    assert np.max(np.abs(sg[rows] - ref)) / scale <= DZ_TOL[s]
+    assert np.max(np.abs(sg - s64)) / scale <= DZ_TOL[s]

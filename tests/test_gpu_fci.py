@@ -166,10 +166,37 @@ def test_davidson_fp64_8e8o_matches_dense_eigh(fci_lib):
     assert abs(r.energy - wv[0]) <= rn * rn / (wv[1] - wv[0]) + 1e-12
 
 
+@pytest.mark.parametrize("n,ne,nch,seed", [(8, 4, 16, 3), (8, 4, 16, 7), (6, 3, 12, 2), (6, 2, 8, 10)])
+def test_davidson_finds_the_lowest_root_outside_the_symmetric_sector(fci_lib, n, ne, nch, seed):
+    """Seeded Hamiltonians whose ground state is antisymmetric under alpha <-> beta string
+    exchange (C[a, b] = -C[b, a]).  The default start (unit vector at min H_II with a
+    pseudo-random admixture) has a component in that sector and the solve returns the
+    lowest eigenvalue of the oracle's dense H with an antisymmetric vector.  The bare
+    closed-shell unit vector (start_mix = 0) is symmetric, so in exact arithmetic the
+    iteration would stay in the symmetric sector; in floating point, rounding seeds the
+    other sector and the solve still ends at an eigenvalue of H (measured: the ground
+    state, for these four Hamiltonians)."""
+    from math import comb
+
+    p = fci_problem(n, ne, ne, n_chol=nch, seed=seed)
+    H = oracle.dense_h(p["hso"], p["gso"], p["dets"]).real
+    w, v = np.linalg.eigh(H)
+    ns = comb(n, ne)
+    v0 = v[:, 0].reshape(ns, ns)
+    assert np.max(np.abs(v0 + v0.T)) < 1e-8  # the ground state is antisymmetric
+    f = gpu_fci(p)
+    r = f.davidson(tol_residual=1e-6, tol_energy=1e-10, max_iter=200)
+    assert r.converged and abs(r.energy - w[0]) < ENERGY_TOL
+    c = r.vector.cpu().numpy().reshape(ns, ns)
+    assert np.max(np.abs(c + c.T)) < 1e-5
+    r0 = f.davidson(tol_residual=1e-6, tol_energy=1e-10, max_iter=200, start_mix=0.0)
+    assert r0.converged and np.min(np.abs(w - r0.energy)) < ENERGY_TOL
+
+
 def test_davidson_gpu_follows_oracle_davidson(fci_lib):
     p = fci_problem(7, 4, 3, seed=21, e_core=-2.0)
     f = gpu_fci(p)
-    r = f.davidson(tol_residual=1e-7, tol_energy=1e-12, max_subspace=6)
+    r = f.davidson(tol_residual=1e-7, tol_energy=1e-12, max_subspace=6, start_mix=0.0)  # the oracle's start
     hd = oracle.diag(p["hso"], p["gso"], p["dets"])
     E, c, log, conv = odav.davidson(lambda v: oracle.sigma(p["hso"], p["gso"], p["dets"], v), hd,
                                     tol_r=1e-7, tol_e=1e-12, max_sub=6, e_shift=p["e_core"])

@@ -415,3 +415,19 @@ def test_davidson_compression_compatible_preconditioner_converges():
     E, c, log, conv = odav.davidson(lambda v: H @ v, hd, tol_r=1e-7, tol_e=1e-12, eps=eps,
                                     max_iter=400)
     assert conv and abs(E - np.linalg.eigvalsh(H)[0]) < 1e-9
+
+
+def test_oracle_sigma_with_a_prebuilt_table_is_the_same_sigma():
+    """The lookup table built once (oracle.SigmaTable, reused across calls, as the benchmark's
+    CPU legs use it) gives the bits of the one-call sigma, on all rows and on a subset."""
+    n, na, nb = 7, 3, 4
+    h, g = synth.real_integrals(n, 9, 23)
+    hso, gso = oracle.spin_orbital_integrals(h, g)
+    dets = oracle.fci_dets(n, na, nb)
+    c = synth.random_vector(len(dets), seed=3)
+    t = oracle.SigmaTable(dets)
+    full = oracle.sigma(hso, gso, dets, c, e_core=0.7)
+    assert np.array_equal(t.sigma(hso, gso, c, e_core=0.7), full)
+    rows = np.array([len(dets) - 1, 0, 17, 17, 400])
+    assert np.array_equal(t.sigma(hso, gso, c, e_core=0.7, rows=rows), full[rows])
+    t.close()
