@@ -49,10 +49,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-davidson", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--serving-requests", type=int, default=32,
-                    help="requests of the serving run (0 = skip); 256 is the full request stream")
-    ap.add_argument("--serving-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
-    ap.add_argument("--no-configs", action="store_true", help="skip the single-sigma runs of the other configs")
+    ap.add_argument("--serving-requests", type=int, default=256, help="requests of the serving run (0 = skip)")
+    ap.add_argument("--serving-rate", type=float, default=0.0,
+                    help="Poisson arrival rate, requests/s; 0 = 1.5 x the single-stream capacity measured in the run")
+    ap.add_argument("--no-configs", action="store_true", help="skip the runs of the other configs")
+    ap.add_argument("--config-repeats", type=int, default=10, help="timed sigma builds per form and config")
     ap.add_argument("--profile-case", default=None,
                     help="only run --steps sigma builds of this workload (a profiling target) and exit")
     ap.add_argument("--path", default=None, choices=["fused", "gemm"],
@@ -269,6 +270,115 @@ def _build_spinor(fci, synth):
     return _build_spinor_named(fci, synth, "spinor_24s12e")
 
 
+def contraction_work(info: dict, n_slices: int, fp64: bool) -> float:
+    """The method's work in one sigma's contraction E = G D (Methods, Eq. sigmaL2e): a
+    dense product of the n_pair x n_pair operator with n_pair x N_K (N_K: determinants,
+    or the intermediate determinants of a DAS layout); 2 flop per multiply-add, 8 per
+    complex one; split precision repeats it for each of the s(s+1)/2 slice products."""
+    npair, nk = info["n_pair"], info["n_det_intermediate"]
+    per = (8.0 if info["dtype"] == 1 else 2.0) * npair * npair * nk
+    return per if fp64 else per * n_slices * (n_slices + 1) / 2
+
+
+def run_config(fci, synth, torch, dev, stream, build, precs, dav, peaks, fp64_peak, repeats):
+    """Repeated sigma builds of one configuration per form (the split forms `repeats` times,
+    FP64 twice when it takes seconds), each with its clocks and the roofline of the
+    contraction kernel, and the time to energy of one mixed-precision solve."""
+    fh = build()
+    Nn = fh.n_det
+    cx = torch.from_numpy(synth.random_vector(Nn, seed=7, complex_=fh.is_complex)).to(dev)
+    info = fh.info
+    row = {"n_det": Nn, "n_det_intermediate": info["n_det_intermediate"], "n_pair": info["n_pair"]}
+    ref_out = None
+    for pr in precs:
+        pname, sl = (pr, 0) if isinstance(pr, str) else pr
+        das_two_pass = info["n_categories"] > 0 and sl >= 4
+        tuned_cfg = (fh.tune(cx, sl, reps=2)["chosen"]
+                     if pname != "fp64" and not fh.is_complex and not das_two_pass else None)
+        o = fh.sigma(cx, precision=pname, n_slices=sl)  # warm-up, workspace
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fh.sigma(cx, precision=pname, n_slices=sl, out=o)
+        e1.record(stream)
+        e1.synchronize()
+        one = e0.elapsed_time(e1)
+        reps = repeats if (pname != "fp64" or one < 200.0) else 2
+        fh.set_phase_timing(True)
+        fh.phase_times(reset=True)
+        clocks = ClockSampler(dev.index or 0)
+        clocks.start()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for ev0, ev1 in evs:
+            ev0.record(stream)
+            fh.sigma(cx, precision=pname, n_slices=sl, out=o)
+            ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ph = fh.phase_times(reset=True)
+        fh.set_phase_timing(False)
+        times = sorted(ev0.elapsed_time(ev1) for ev0, ev1 in evs)
+        ms = statistics.median(times)
+        key = pname if pname == "fp64" else f"{pname}_s{sl}"
+        rec = {"ms": ms, "repeats": reps, "ms_min": times[0], "ms_max": times[-1],
+               "det_sigma_per_s": Nn / (ms * 1e-3), "clocks": clk,
+               "phases_ms": {k: v["ms"] / reps for k, v in ph.items()}}
+        if tuned_cfg:
+            rec["tuned"] = tuned_cfg
+        if pname == "fp64":
+            ref_out = o.clone()
+        elif ref_out is not None:
+            fh.sync_status()
+            rec["rel_err_vs_fp64"] = ((o - ref_out).abs().max() / ref_out.abs().max()).item()
+        cms = ph["contract"]["ms"] / max(ph["contract"]["launches"], 1)
+        work = contraction_work(info, sl, pname == "fp64")
+        launches_per_sigma = ph["contract"]["launches"] / reps
+        ach = work / launches_per_sigma / (cms * 1e-3) / 1e12 if cms > 0 else None
+        if pname == "fp64":
+            rec["roofline"] = {"bound": "alu", "kernel": "FP64 contraction (SIMT FMA)", "achieved": ach,
+                               "peak": fp64_peak, "unit": "TFLOP/s",
+                               "frac": ach / fp64_peak if (ach and fp64_peak) else None,
+                               "peak_source": "cuBLAS DGEMM 4096^3 measured in this run"}
+        else:
+            pk = peaks.get("bf16_tflops", 1891.0)
+            rec["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                               "frac": ach / pk if ach else None,
+                               "kernel": ("k_oz_gemm (two-pass DAS)" if das_two_pass else
+                                          "k_oz_das (fused DAS)" if info["n_categories"] > 0 else
+                                          "k_oz_gemm (complex, real embedding)" if fh.is_complex else
+                                          "alpha/beta split contraction"),
+                               "flops_counted": "algorithmic: the contraction's multiply-adds over n_pair x n_pair x "
+                                                "N_K, times s(s+1)/2 slice products",
+                               "contraction_launches_per_sigma": launches_per_sigma,
+                               "peak_source": "MEASURED_PEAKS.json bf16_tflops, burst (of measured)"}
+            s64 = row.get("fp64")
+            if s64:
+                rec["speedup_vs_fp64"] = s64["ms"] / ms
+        row[key] = rec
+    if dav is not None:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fh.davidson(max_iter=200, tol_residual=1e-5, tol_energy=1e-9, **dav)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        d = {"form": f"s={dav['n_slices']} until ||r|| <= {dav['switch_residual']}, then s={dav['final_slices']}",
+             "seconds": secs, "energy": r.energy, "converged": r.converged, "iterations": len(r.iterations),
+             "sigma_builds": r.n_sigma}
+        f64 = row.get("fp64")
+        if f64:
+            # the FP64 solve is not run here (minutes): its time is extrapolated as as many
+            # sigma builds as the mixed solve took, each at the measured FP64 sigma time (a
+            # lower bound: the Davidson vector work of the FP64 solve is left out)
+            d["fp64_extrapolated_seconds"] = r.n_sigma * f64["ms"] * 1e-3
+            d["speedup_vs_fp64_extrapolated"] = d["fp64_extrapolated_seconds"] / secs
+            d["extrapolation"] = "FP64 solve >= sigma builds of the mixed solve x measured FP64 sigma time"
+        row["time_to_energy"] = d
+    fh.close()
+    del cx, o, ref_out
+    return row
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(a, rank, world, local_rank):
@@ -425,77 +535,30 @@ def run_ours(a, rank, world, local_rank):
                 d["energy_error_vs_fp64"] = abs(d["energy"] - e64)
                 d["speedup_vs_fp64"] = davidson["fp64"]["seconds"] / d["seconds"]
 
-    # one sigma of each other configuration (parity-tested layouts), FP64 and split
+    # every other configuration (parity-tested layouts), FP64 and split: repeated sigma
+    # builds with a clock record and the roofline of the contraction, then the time to
+    # energy of the mixed-precision solve
     config_runs = None
     if not a.no_configs and rank == 0:
         config_runs = {}
         del flush
         torch.cuda.empty_cache()
-        for name, build, precs in (
-                ("fci_8e8o", lambda: _build_fci(fci, synth, "fci_8e8o"), ("fp64", ("oz_bf16", 6))),
+        peaks = _peaks()
+        for name, build, precs, dav in (
+                ("fci_8e8o", lambda: _build_fci(fci, synth, "fci_8e8o"), ("fp64", ("oz_bf16", 6)), None),
                 ("das_16o_4x4_16e_t2", lambda: _build_das(fci, synth, "das_16o_4x4", 8),
-                 ("fp64", ("oz_bf16", 2), ("oz_bf16", 3))),
+                 ("fp64", ("oz_bf16", 2), ("oz_bf16", 3), ("oz_bf16", 6)),
+                 dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4, final_precision="oz_bf16",
+                      final_slices=6)),
                 ("das_16o_4x4_8e_t1", lambda: _build_das(fci, synth, "das_16o_4x4_8e", 4),
-                 ("fp64", ("oz_bf16", 3))),
-                ("spinor_24s12e", lambda: _build_spinor(fci, synth), ("fp64", ("oz_bf16", 3), ("oz_bf16", 8)))):
+                 ("fp64", ("oz_bf16", 3), ("oz_bf16", 6)), None),
+                ("spinor_24s12e", lambda: _build_spinor(fci, synth), ("fp64", ("oz_bf16", 3), ("oz_bf16", 8)),
+                 dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4, final_precision="oz_bf16",
+                      final_slices=8))):
             try:
-                fh = build()
-                Nn = fh.n_det
-                cx = torch.from_numpy(synth.random_vector(Nn, seed=7, complex_=fh.is_complex)).to(dev)
-                row = {"n_det": Nn, "n_det_intermediate": fh.info["n_det_intermediate"], "n_pair": fh.info["n_pair"]}
-                ref_out = None
-                for pr in precs:
-                    pname, sl = (pr, 0) if isinstance(pr, str) else pr
-                    tuned_cfg = fh.tune(cx, sl, reps=2)["chosen"] if pname != "fp64" and not fh.is_complex else None
-                    o = fh.sigma(cx, precision=pname, n_slices=sl)  # warm-up, workspace
-                    torch.cuda.synchronize()
-                    fh.set_phase_timing(True)
-                    fh.phase_times(reset=True)
-                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    fh.sigma(cx, precision=pname, n_slices=sl, out=o)
-                    e1.record(stream)
-                    e1.synchronize()
-                    ph = fh.phase_times(reset=True)
-                    fh.set_phase_timing(False)
-                    ms = e0.elapsed_time(e1)
-                    key = pname if pname == "fp64" else f"{pname}_s{sl}"
-                    cms = ph["contract"]["ms"]
-                    m_rows = row["n_pair"]
-                    flops = (8.0 if fh.is_complex else 2.0) * m_rows * m_rows * row["n_det_intermediate"]
-                    rec = {"ms": ms, "det_sigma_per_s": Nn / (ms * 1e-3),
-                           "phases_ms": {k: v["ms"] for k, v in ph.items()}}
-                    if tuned_cfg:
-                        rec["tuned"] = tuned_cfg
-                    if pname == "fp64":
-                        ref_out = o.clone()
-                    elif ref_out is not None:
-                        fh.sync_status()
-                        rec["rel_err_vs_fp64"] = ((o - ref_out).abs().max() / ref_out.abs().max()).item()
-                    if pname == "fp64":
-                        rec["contract_tflops"] = flops / (cms * 1e-3) / 1e12 if cms > 0 else None
-                        rec["contract_frac_of_fp64_peak"] = (rec["contract_tflops"] / fp64_peak
-                                                             if (cms > 0 and fp64_peak) else None)
-                    else:
-                        # executed MMA work of the split kernels (padded shapes, s(s+1)/2 products)
-                        kp = -(-m_rows // 16) * 16
-                        if fh.is_complex:  # real embedding: M = K = 2 n^2 (padded to 128 / 32), 64-det tiles
-                            ex = 2.0 * (-(-2 * m_rows // 128) * 128) * (-(-2 * m_rows // 32) * 32) * (-(-Nn // 64) * 64)
-                        elif fh.info["n_categories"] > 0:  # DAS: 128-determinant tiles x N = K = padded pairs
-                            ex = 2.0 * (-(-row["n_det_intermediate"] // 128) * 128) * kp * kp
-                        else:  # alpha/beta: M = 128 pair rows, 64-determinant tiles
-                            ex = 2.0 * 128 * kp * (-(-Nn // 64) * 64)
-                        ex *= sl * (sl + 1) / 2
-                        rec["contract_tflops_executed"] = ex / (cms * 1e-3) / 1e12 if cms > 0 else None
-                        rec["contract_frac_of_bf16_sustained"] = (rec["contract_tflops_executed"] / _peaks().get("bf16_tflops_sustained", 1700.0)
-                                                                  if cms > 0 else None)
-                        s64 = row.get("fp64")
-                        if s64:
-                            rec["speedup_vs_fp64"] = s64["ms"] / ms
-                    row[key] = rec
+                row = run_config(fci, synth, torch, dev, stream, build, precs, dav, peaks, fp64_peak,
+                                 a.config_repeats)
                 config_runs[name] = row
-                fh.close()
-                del cx, o, ref_out
                 torch.cuda.empty_cache()
             except Exception as e:  # report, do not abort the benchmark
                 config_runs[name] = {"unavailable": str(e)[:200]}
@@ -549,10 +612,18 @@ def run_ours(a, rank, world, local_rank):
     if a.serving_requests > 0 and rank == 0:
         from paper_2505_20375_gb300 import serving
 
-        reqs = serving.make_requests(a.serving_requests, rate=a.serving_rate, seed=5)
-        res, serving_stats = serving.Server(device=local_rank, max_active=16).run(reqs)
-        serving_stats["request_mix"] = "uniform over FCI(6e,6o),(8e,8o),(10e,10o),(12e,12o), DAS 4x4 orbitals 4a4b <=1 transfer"
-        serving_stats["rate_per_s"] = a.serving_rate
+        srv = serving.Server(device=local_rank, max_active=64)
+        rate, cap = a.serving_rate, None
+        if rate <= 0:  # 1.5 x the single-stream capacity of the mix, measured here
+            mean_s, per = serving.measure_capacity(srv)
+            rate = 1.5 / mean_s
+            cap = {"mean_service_s": mean_s, "requests_per_s": 1.0 / mean_s, "alone_s": per}
+        reqs = serving.make_requests(a.serving_requests, rate=rate, seed=5)
+        res, serving_stats = srv.run(reqs)
+        serving_stats["request_mix"] = ("uniform over FCI(6e,6o),(8e,8o),(10e,10o),(12e,12o), DAS 4x4 orbitals 4a4b "
+                                        "<=1 transfer; half FP64, half mixed (3 slices, then 6 / the two-pass DAS form)")
+        serving_stats["rate_per_s"] = rate
+        serving_stats["single_stream_capacity"] = cap
         serving_stats["metric"] = "time from arrival to converged energy (|dE| <= 1e-9, ||r|| <= 1e-5)"
         mixed = [r.latency for r in res if r.mixed]
         plain = [r.latency for r in res if not r.mixed]

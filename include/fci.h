@@ -151,10 +151,13 @@ int fci_sigma_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slic
  *   precision: FCI_PREC_FP64, or FCI_PREC_OZ_BF16 with n_slices 16-bit digit slices of
  *             each operand of the contraction: alpha/beta strings (R64) take 2..7
  *             slices (n_orb <= 15; 6 and 7 reach the FP64 tolerance); the DAS layout
- *             takes 2 or 3 slices (n_orb <= 17), with E stored in FP32, for the first
- *             phase of a mixed-precision solve; spinor strings with complex integrals
- *             take 2..8 slices of 7 bits (8 reaches the FP64 tolerance);
- *             FCI_ERR_UNSUPPORTED otherwise;
+ *             takes 2 or 3 slices (n_orb <= 17; one fused kernel, E stored in FP32, for
+ *             the first phase of a mixed-precision solve) or 4 and more while
+ *             n_slices x n_pair <= 1023 (two passes: a digit image of D, then the
+ *             bulk-copy GEMM with exact int64 E; 6 and 7 reach the FP64 tolerance, the
+ *             workspace holds up to 96 GiB of E and 24 GiB of digit image); spinor
+ *             strings with complex integrals take 2..8 slices of 7 bits (8 reaches the
+ *             FP64 tolerance); FCI_ERR_UNSUPPORTED otherwise;
  *   workspace: DEVICE pointer, >= fci_sigma_workspace_bytes, 256-byte aligned.
  * Asynchronous on `stream`. */
 int fci_sigma(fci_handle h, const void *C, void *sigma, int n_vec, int precision,
@@ -178,7 +181,8 @@ typedef struct {
     int use_guess;          /* 1: start from C_io; 0: unit vector at min H_II */
     int final_precision;    /* sigma after the switch: FCI_PREC_FP64 (default), or
                                FCI_PREC_OZ_BF16 with final_slices >= 6 (error below
-                               1e-11 of ||sigma||, the FP64 parity bar) */
+                               1e-11 of ||sigma||, the FP64 parity bar; on the DAS
+                               layout the two-pass split form) */
     int final_slices;
     int gap_bound;          /* 1: after convergence, keep the subspace and converge the
                                second Ritz pair as well (until ||r_1|| <= max(tol_residual,
@@ -370,6 +374,32 @@ int fci_set_phase_timing(fci_handle h, int enable);
  * in milliseconds (ms[FCI_N_PHASES]) and the number of kernel launches
  * (launches[FCI_N_PHASES]); either pointer may be NULL.  reset != 0 clears the sums. */
 int fci_get_phase_times(fci_handle h, double *ms, int64_t *launches, int reset);
+
+/* ------------------------------------------------ categorically compressed sigma */
+
+/* sigma = H C on the DAS layout for a categorically compressed C (Results: categorical
+ * compression, C = (+)_B (V^B, A^B), the nonzero coefficients of each category and their
+ * addresses in a compressed sparse column; Methods, Algorithm 1 and the compression-
+ * preservation argument: only nonzero coefficients contribute and sigma comes out
+ * compressed).  Both vectors are given as DAS addresses in ascending order with their
+ * values, i.e. the per-category (V, A) arrays of the paper concatenated in category order
+ * (a category's local address is its DAS address minus the category's offset).
+ *   c_addr, c_val: DEVICE, nnz_c entries: ascending target addresses (< info.n_det) and
+ *                  their coefficients (explicit zeros allowed);
+ *   out_addr, out_val: DEVICE, capacity entries: sigma on its structural support (every
+ *                  target determinant that H connects to a nonzero C_K), ascending; the
+ *                  values equal the FP64 sigma of the dense vector there, term by term in
+ *                  the same order, and the dense sigma is zero elsewhere;
+ *   *nnz_sigma:    HOST, receives the size of the support (also when capacity is too small,
+ *                  which returns FCI_ERR_ARG);
+ *   workspace:     DEVICE, >= fci_sigma_compressed_workspace_bytes(h, nnz_c), 256-byte
+ *                  aligned (bounded by nnz_c x (moves per determinant)^2 support entries).
+ * Real integrals only.  FCI_ERR_ARG for addresses that are not ascending target addresses.
+ * Host-synchronous. */
+int fci_sigma_compressed_workspace_bytes(fci_handle h, int64_t nnz_c, size_t *bytes);
+int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_val, int64_t nnz_c,
+                         int64_t *out_addr, double *out_val, int64_t capacity, int64_t *nnz_sigma,
+                         void *workspace, size_t workspace_bytes, fci_stream stream);
 
 /* ------------------------------------------------------- allocation-free sigma */
 

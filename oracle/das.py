@@ -87,3 +87,46 @@ def das_dets(spaces, ref_a, ref_b, n_a, n_b, max_transfer):
         k += len(blk)
     assert k == total
     return out, cats
+
+
+def dets_of_addresses(spaces, ref_a, ref_b, n_a, n_b, max_transfer, addrs):
+    """Spin-orbital masks of the DAS determinants at the given addresses, decoded from the
+    definition of the canonical order above (category by offset, then row-major
+    [alpha-local][beta-local], each local index a mixed-radix number over the spaces, space
+    1 most significant, digits the ranks of the spaces' sub-strings); for spaces too large
+    to enumerate whole."""
+    n = sum(spaces)
+    cats, total = categories(spaces, ref_a, ref_b, n_a, n_b, max_transfer)
+    offs = [c[4] for c in cats]
+    space_off = np.cumsum([0] + list(spaces[:-1]))
+    sub = {}
+
+    def substrings(m, k):
+        if (m, k) not in sub:
+            sub[(m, k)] = _space_strings(m, k)
+        return sub[(m, k)]
+
+    def string_of(p, local):
+        digits = []
+        for m, k in reversed(list(zip(spaces, p))):
+            r = comb(m, k)
+            digits.append(local % r)
+            local //= r
+        digits.reverse()
+        v = 0
+        for (m, k), d, o in zip(zip(spaces, p), digits, space_off):
+            v |= substrings(m, k)[d] << int(o)
+        return v
+
+    import bisect
+
+    out = np.empty(len(addrs), np.uint64)
+    for i, x in enumerate(addrs):
+        x = int(x)
+        if not 0 <= x < total:
+            raise ValueError("address outside the DAS space")
+        c = bisect.bisect_right(offs, x) - 1
+        a, b, na, nb, off = cats[c]
+        la, lb = divmod(x - off, nb)
+        out[i] = string_of(a, la) | (string_of(b, lb) << n)
+    return out

@@ -1,0 +1,445 @@
+// Categorically compressed sigma on the STP-DAS layout (Results: categorical compression,
+// the CI vector as a direct sum of per-category compressed vectors (V^B, A^B) holding only
+// the nonzero coefficients and their addresses; Methods, Algorithm 1 and the compression-
+// preservation argument: only nonzero coefficients contribute, and sigma comes out
+// compressed as well).
+//
+// The paper's CPU algorithm intersects, for every intermediate determinant J, the sorted
+// excitation list of J with the sorted addresses of the nonzero coefficients (exponential
+// search), and accumulates sigma in per-category hash tables.  On the GPU the same
+// restriction to nonzero coefficients is reached from the other side, with no search:
+//   1. every nonzero C_K emits its single replacements J = E_sr K (alpha and beta moves
+//      from the string tables), which are the only intermediate determinants whose
+//      D[rs, J] = sum_K <J|E_rs|K> C_K can be nonzero; a hash table gives each distinct J a
+//      column, and D[rs, column] collects the (at most two: one alpha, one beta) terms;
+//   2. E = G D over those columns only (the dense FP64 contraction of the other paths);
+//   3. every column J emits its single replacements L inside the target space: the
+//      structural support of sigma, made distinct by a second hash table and sorted
+//      (radix sort on the address), which is the compressed output order;
+//   4. sigma_L = sum_pq <L|E_pq|J> E[pq, J] + e_core C_L for every L of the support,
+//      gathering over L's replacements in pair order (alpha then beta), looking each J up
+//      in the first table (absent J have E = 0): the arithmetic and its order are those of
+//      the dense FP64 DAS path, so the result equals the dense sigma on the support and
+//      the dense sigma is zero elsewhere.
+// Hash tables use open addressing with linear probing over a power-of-two capacity of at
+// least twice the largest number of keys, so no probe sequence runs past a free slot; every
+// probe loop is bounded by the capacity all the same and reports an overflow instead.
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "das_dev.cuh"
+
+namespace {
+
+using das_dev::das_addr;
+using das_dev::das_strings;
+using das_dev::DasDev;
+using das_dev::make_dev;
+
+constexpr unsigned long long HT_EMPTY = ~0ull;
+constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS;  // radix sort tile
+
+inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+__device__ __forceinline__ uint64_t hmix(uint64_t z) {  // splitmix64 finaliser (published constants)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Insert key k (>= 0) once.  Returns false if every slot was probed (cannot happen at
+// the capacities used; reported as an overflow).
+__device__ bool ht_insert(unsigned long long *keys, uint64_t mask, uint64_t k) {
+    uint64_t p = hmix(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long old = atomicCAS(keys + p, HT_EMPTY, (unsigned long long)k);
+        if (old == HT_EMPTY || old == k) return true;
+        p = (p + 1) & mask;
+    }
+    return false;
+}
+
+// Column of key k, or -1 if k is not in the table.
+__device__ int64_t ht_find(const unsigned long long *__restrict__ keys, const int32_t *__restrict__ cols, uint64_t mask,
+                           uint64_t k) {
+    uint64_t p = hmix(k) & mask;
+    for (uint64_t probe = 0; probe <= mask; ++probe) {
+        const unsigned long long v = keys[p];
+        if (v == k) return cols[p];
+        if (v == HT_EMPTY) return -1;
+        p = (p + 1) & mask;
+    }
+    return -1;
+}
+
+struct CsArgs {
+    DasDev d;
+    int n_cat_int, nent_a, nent_b, npair;
+    const uint64_t *rep_a, *rep_b;   // packed replacement lists [n_str][n_ent]
+    const int32_t *pair_a, *pair_b;  // dense pair tables [n_pair_pad][n_str]: (T << 1) | sign, or -1
+    const int64_t *c_addr;
+    const double *c_val;
+    int64_t nnz_c;
+    unsigned long long *hj;          // intermediate determinants J
+    int32_t *hj_col;
+    uint64_t hj_mask;
+    int64_t *j_addr;                 // [n1]: the J of each column
+    double *D, *E;                   // [n_pair][ldd]
+    int64_t ldd;
+    unsigned long long *hl;          // target determinants L of the support
+    uint64_t hl_mask;
+    int64_t *l_addr;                 // [n2]
+    unsigned long long *counts;      // [0]: columns n1, [1]: support n2, [2]: overflow flag
+    double e_core;
+};
+
+// Step 1: every move of every nonzero C_K.  pass 0 inserts J; pass 1 adds sign C_K to
+// D[pair, column(J)].
+__global__ void __launch_bounds__(256) k_cs_expand(const __grid_constant__ CsArgs a, int pass) {
+    const int nm = a.nent_a + a.nent_b;
+    const int64_t total = a.nnz_c * nm;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / nm;
+        const int m = (int)(t - i * nm);
+        int32_t A, B;
+        int pb;
+        das_strings(a.d, a.d.n_cat, a.c_addr[i], A, B, pb);
+        uint64_t e;
+        int64_t J;
+        if (m < a.nent_a) {
+            e = a.rep_a[(int64_t)A * a.nent_a + m];
+            J = das_addr(a.d, (int32_t)rep_target(e), B);
+        } else {
+            e = a.rep_b[(int64_t)B * a.nent_b + (m - a.nent_a)];
+            J = das_addr(a.d, A, (int32_t)rep_target(e));
+        }
+        if (J < 0) continue;
+        if (pass == 0) {
+            if (!ht_insert(a.hj, a.hj_mask, (uint64_t)J)) atomicExch(a.counts + 2, 1ull);
+        } else {
+            const int64_t col = ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J);
+            if (col < 0) continue;
+            const double c = a.c_val[i];
+            atomicAdd(a.D + (int64_t)rep_pair(e) * a.ldd + col, rep_neg(e) ? -c : c);
+        }
+    }
+}
+
+// Distinct keys of a table get consecutive columns.
+__global__ void k_cs_compact(unsigned long long *keys, int32_t *cols, uint64_t cap, int64_t *addr,
+                             unsigned long long *counter) {
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < cap; p += (uint64_t)gridDim.x * blockDim.x) {
+        const unsigned long long k = keys[p];
+        if (k == HT_EMPTY) continue;
+        const unsigned long long c = atomicAdd(counter, 1ull);
+        if (cols) cols[p] = (int32_t)c;
+        addr[c] = (int64_t)k;
+    }
+}
+
+// Step 3: the target determinants one move away from a column J.
+__global__ void __launch_bounds__(256) k_cs_support(const __grid_constant__ CsArgs a, int64_t n1) {
+    const int nm = a.nent_a + a.nent_b;
+    const int64_t total = n1 * nm;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / nm;
+        const int m = (int)(t - j * nm);
+        int32_t A, B;
+        int pb;
+        das_strings(a.d, a.n_cat_int, a.j_addr[j], A, B, pb);
+        int64_t L;
+        if (m < a.nent_a) L = das_addr(a.d, (int32_t)rep_target(a.rep_a[(int64_t)A * a.nent_a + m]), B);
+        else L = das_addr(a.d, A, (int32_t)rep_target(a.rep_b[(int64_t)B * a.nent_b + (m - a.nent_a)]));
+        if (L < 0 || L >= a.d.n_det) continue;
+        if (!ht_insert(a.hl, a.hl_mask, (uint64_t)L)) atomicExch(a.counts + 2, 1ull);
+    }
+}
+
+// Step 4: sigma on the sorted support, in the dense DAS path's order of terms.
+__global__ void __launch_bounds__(256) k_cs_sigma(const __grid_constant__ CsArgs a, const int64_t *__restrict__ l_sorted,
+                                                  int64_t n2, double *__restrict__ out_val) {
+    for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n2; o += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = l_sorted[o];
+        int32_t A, B;
+        int pb;
+        das_strings(a.d, a.d.n_cat, L, A, B, pb);
+        double acc = 0.0;
+        for (int pp = 0; pp < a.npair; ++pp) {
+            const double *Ep = a.E + (int64_t)pp * a.ldd;
+            const int32_t ea = __ldg(a.pair_a + (int64_t)pp * a.d.nsa + A);
+            if (ea >= 0) {
+                const int64_t J = das_addr(a.d, ea >> 1, B);
+                const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
+                if (col >= 0) {
+                    const double e = Ep[col];
+                    acc += (ea & 1) ? -e : e;
+                }
+            }
+            const int32_t eb = __ldg(a.pair_b + (int64_t)pp * a.d.nsb + B);
+            if (eb >= 0) {
+                const int64_t J = das_addr(a.d, A, eb >> 1);
+                const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
+                if (col >= 0) {
+                    const double e = Ep[col];
+                    acc += (eb & 1) ? -e : e;
+                }
+            }
+        }
+        // C_L from the sorted nonzero addresses (binary search)
+        double cl = 0.0;
+        int64_t lo = 0, hi = a.nnz_c - 1;
+        while (lo <= hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            const int64_t v = a.c_addr[mid];
+            if (v == L) { cl = a.c_val[mid]; break; }
+            if (v < L) lo = mid + 1; else hi = mid - 1;
+        }
+        out_val[o] = fma(a.e_core, cl, acc);  // as the dense FP64 scatter
+    }
+}
+
+// ------------------------------------------------------------------ LSD radix sort
+// 8-bit digits, ascending, stable; one tile = RS_TILE keys.  Histograms per tile and
+// digit, an exclusive scan over (digit, tile), then a stable scatter: inside a tile the
+// keys keep their order (rounds of 256 keys; within a round, warps in order and lanes in
+// order, ranks from __match_any_sync).
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                                                        int64_t ntiles, unsigned long long *__restrict__ counts) {
+    __shared__ unsigned int h[256];
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        h[threadIdx.x] = 0;
+        __syncthreads();
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            const int64_t idx = tile * RS_TILE + r * RS_THREADS + threadIdx.x;
+            if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255], 1u);
+        }
+        __syncthreads();
+        counts[(int64_t)threadIdx.x * ntiles + tile] = h[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+// Exclusive scan of m counts in one block of 1024 threads (each a contiguous run).
+__global__ void __launch_bounds__(1024) k_rs_scan(unsigned long long *__restrict__ c, int64_t m) {
+    __shared__ unsigned long long part[1024];
+    const int64_t per = (m + 1023) / 1024, b = threadIdx.x * per, e = min(m, b + per);
+    unsigned long long s = 0;
+    for (int64_t i = b; i < e; ++i) s += c[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
+        const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = threadIdx.x ? part[threadIdx.x - 1] : 0ull;
+    for (int64_t i = b; i < e; ++i) {
+        const unsigned long long v = c[i];
+        c[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint64_t *__restrict__ in, uint64_t *__restrict__ out,
+                                                           int64_t n, int shift, int64_t ntiles,
+                                                           const unsigned long long *__restrict__ base) {
+    __shared__ unsigned int run[256];
+    __shared__ unsigned int wc[RS_THREADS / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        run[threadIdx.x] = 0;
+        for (int r = 0; r < RS_ITEMS; ++r) {
+            for (int w = 0; w < RS_THREADS / 32; ++w) wc[w][threadIdx.x] = 0;
+            __syncthreads();
+            const int64_t idx = tile * RS_TILE + r * RS_THREADS + threadIdx.x;
+            const bool valid = idx < n;
+            const uint64_t key = valid ? in[idx] : 0;
+            const unsigned dg = valid ? (unsigned)((key >> shift) & 255) : 256u + lane;  // invalid lanes match no one
+            const unsigned peers = __match_any_sync(0xFFFFFFFFu, dg);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            if (valid && rank == 0) wc[warp][dg] = __popc(peers);
+            __syncthreads();
+            if (valid) {
+                unsigned off = run[dg] + rank;
+                for (int w = 0; w < warp; ++w) off += wc[w][dg];
+                out[base[(int64_t)dg * ntiles + tile] + off] = key;
+            }
+            __syncthreads();
+            unsigned add = 0;
+            for (int w = 0; w < RS_THREADS / 32; ++w) add += wc[w][threadIdx.x];
+            run[threadIdx.x] += add;
+            __syncthreads();
+        }
+    }
+}
+
+unsigned grid_of(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 32)); }
+
+uint64_t pow2_at_least(uint64_t x) {
+    uint64_t c = 1024;
+    while (c < x) c <<= 1;
+    return c;
+}
+
+// Sizes of the compressed sigma's buffers for nnz_c nonzero coefficients: columns and
+// support are bounded by the number of moves; hash tables hold twice their bound.
+struct CsSizes {
+    int64_t n1max, n2max;
+    uint64_t capj, capl;
+    int64_t ntiles;
+    size_t bytes;
+    size_t off_hj, off_hjc, off_jaddr, off_D, off_E, off_hl, off_laddr, off_tmp, off_cnt, off_hist;
+};
+
+CsSizes cs_sizes(const fci_context *h, int64_t nnz_c) {
+    CsSizes z;
+    const int64_t nm = h->nent_a + h->nent_b;
+    z.n1max = std::max<int64_t>(1, nnz_c * nm);
+    z.n2max = std::max<int64_t>(1, z.n1max * nm);
+    z.capj = pow2_at_least((uint64_t)(2 * z.n1max));
+    z.capl = pow2_at_least((uint64_t)(2 * z.n2max));
+    z.ntiles = ceil_div(z.n2max, RS_TILE);
+    size_t o = 0;
+    z.off_hj = o; o += al(z.capj * 8);
+    z.off_hjc = o; o += al(z.capj * 4);
+    z.off_jaddr = o; o += al((size_t)z.n1max * 8);
+    z.off_D = o; o += al((size_t)h->npair * z.n1max * 8);
+    z.off_E = o; o += al((size_t)h->npair * z.n1max * 8);
+    z.off_hl = o; o += al(z.capl * 8);
+    z.off_laddr = o; o += al((size_t)z.n2max * 8);
+    z.off_tmp = o; o += al((size_t)z.n2max * 8);
+    z.off_hist = o; o += al((size_t)256 * z.ntiles * 8);
+    z.off_cnt = o; o += 256;
+    z.bytes = o;
+    return z;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fci_sigma_compressed_workspace_bytes(fci_handle h, int64_t nnz_c, size_t *bytes) {
+    if (!h || !bytes || nnz_c < 0) return fci_fail(h, FCI_ERR_ARG, "bad argument");
+    if (!h->das_active) return fci_fail(h, FCI_ERR_STATE, "compressed sigma needs the DAS layout");
+    *bytes = cs_sizes(h, nnz_c).bytes;
+    return FCI_OK;
+}
+
+int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_val, int64_t nnz_c, int64_t *out_addr,
+                         double *out_val, int64_t capacity, int64_t *nnz_sigma, void *ws, size_t ws_bytes,
+                         fci_stream stream) {
+    if (!h) return fci_fail(nullptr, FCI_ERR_ARG, "NULL handle");
+    if (!h->das_active) return fci_fail(h, FCI_ERR_STATE, "compressed sigma needs the DAS layout");
+    if (h->dtype != FCI_R64) return fci_fail(h, FCI_ERR_UNSUPPORTED, "compressed sigma is built for real integrals");
+    if (!nnz_sigma || nnz_c < 0 || capacity < 0 || (nnz_c && (!c_addr || !c_val)) || (capacity && (!out_addr || !out_val)))
+        return fci_fail(h, FCI_ERR_ARG, "bad compressed-vector arguments");
+    const CsSizes z = cs_sizes(h, nnz_c);
+    if (!ws || ws_bytes < z.bytes || ((uintptr_t)ws & 255))
+        return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes or misaligned", ws_bytes, z.bytes);
+    if (z.n1max >= ((int64_t)1 << 31)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "too many nonzero coefficients");
+    FCI_CUDA(h, cudaSetDevice(h->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    *nnz_sigma = 0;
+    if (nnz_c == 0) return FCI_OK;
+    // the addresses must be ascending target addresses (checked on the device copy)
+    std::vector<int64_t> hc(nnz_c);
+    FCI_CUDA(h, cudaMemcpyAsync(hc.data(), c_addr, nnz_c * 8, cudaMemcpyDeviceToHost, s));
+    FCI_CUDA(h, cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < nnz_c; ++i)
+        if (hc[i] < 0 || hc[i] >= h->das.n_det || (i && hc[i] <= hc[i - 1]))
+            return fci_fail(h, FCI_ERR_ARG, "compressed C: addresses must be ascending target addresses");
+    char *w = (char *)ws;
+    CsArgs a;
+    a.d = make_dev(h);
+    a.n_cat_int = h->das.n_cat_int;
+    a.nent_a = h->nent_a;
+    a.nent_b = h->nent_b;
+    a.npair = h->npair;
+    a.rep_a = h->d_rep_a;
+    a.rep_b = h->d_rep_b;
+    a.pair_a = h->d_pair_a;
+    a.pair_b = h->d_pair_b;
+    a.c_addr = c_addr;
+    a.c_val = c_val;
+    a.nnz_c = nnz_c;
+    a.hj = (unsigned long long *)(w + z.off_hj);
+    a.hj_col = (int32_t *)(w + z.off_hjc);
+    a.hj_mask = z.capj - 1;
+    a.j_addr = (int64_t *)(w + z.off_jaddr);
+    a.D = (double *)(w + z.off_D);
+    a.E = (double *)(w + z.off_E);
+    a.ldd = z.n1max;
+    a.hl = (unsigned long long *)(w + z.off_hl);
+    a.hl_mask = z.capl - 1;
+    a.l_addr = (int64_t *)(w + z.off_laddr);
+    a.counts = (unsigned long long *)(w + z.off_cnt);
+    a.e_core = h->e_core;
+    unsigned long long cnt[3] = {0, 0, 0};
+    // 1. the intermediate determinants one move from a nonzero coefficient, and D on them
+    {
+        phase_scope ps(h, s, FCI_PHASE_GATHER, 4);
+        FCI_CUDA(h, cudaMemsetAsync(a.hj, 0xFF, z.capj * 8, s));
+        FCI_CUDA(h, cudaMemsetAsync(a.counts, 0, 256, s));
+        const int64_t moves = nnz_c * (a.nent_a + a.nent_b);
+        k_cs_expand<<<grid_of(moves), 256, 0, s>>>(a, 0);
+        k_cs_compact<<<grid_of((int64_t)z.capj), 256, 0, s>>>(a.hj, a.hj_col, z.capj, a.j_addr, a.counts);
+        FCI_CUDA(h, cudaMemcpyAsync(cnt, a.counts, sizeof cnt, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(h, cudaStreamSynchronize(s));
+        if (cnt[2]) return fci_fail(h, FCI_ERR_CUDA, "compressed sigma: hash table overflow");
+        FCI_CUDA(h, cudaMemsetAsync(a.D, 0, (size_t)h->npair * z.n1max * 8, s));
+        k_cs_expand<<<grid_of(moves), 256, 0, s>>>(a, 1);
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    const int64_t n1 = (int64_t)cnt[0];
+    // 2. E = G D on the n1 columns
+    {
+        phase_scope ps(h, s, FCI_PHASE_CONTRACT, 1);
+        FCI_CUDA(h, launch_dgemm(h->npair, n1, h->npair, h->d_G, a.D, z.n1max, a.E, z.n1max, s));
+    }
+    // 3. the support of sigma, distinct and sorted
+    {
+        phase_scope ps(h, s, FCI_PHASE_OTHER, 3);
+        FCI_CUDA(h, cudaMemsetAsync(a.hl, 0xFF, z.capl * 8, s));
+        k_cs_support<<<grid_of(n1 * (a.nent_a + a.nent_b)), 256, 0, s>>>(a, n1);
+        k_cs_compact<<<grid_of((int64_t)z.capl), 256, 0, s>>>(a.hl, nullptr, z.capl, a.l_addr, a.counts + 1);
+        FCI_CUDA(h, cudaMemcpyAsync(cnt, a.counts, sizeof cnt, cudaMemcpyDeviceToHost, s));
+        FCI_CUDA(h, cudaStreamSynchronize(s));
+        if (cnt[2]) return fci_fail(h, FCI_ERR_CUDA, "compressed sigma: hash table overflow");
+    }
+    const int64_t n2 = (int64_t)cnt[1];
+    *nnz_sigma = n2;
+    if (n2 > capacity)
+        return fci_fail(h, FCI_ERR_ARG, "output capacity %lld < %lld support entries", (long long)capacity, (long long)n2);
+    uint64_t *src = (uint64_t *)a.l_addr, *dst = (uint64_t *)(w + z.off_tmp);
+    {
+        phase_scope ps(h, s, FCI_PHASE_OTHER, 1);
+        int bits = 1;
+        while (bits < 63 && ((uint64_t)1 << bits) < (uint64_t)h->das.n_det) ++bits;
+        const int64_t nt = ceil_div(n2, RS_TILE);
+        unsigned long long *hist = (unsigned long long *)(w + z.off_hist);
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, 152 * 8));
+        for (int shift = 0; shift < bits; shift += 8) {
+            k_rs_hist<<<g, RS_THREADS, 0, s>>>(src, n2, shift, nt, hist);
+            k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * nt);
+            k_rs_scatter<<<g, RS_THREADS, 0, s>>>(src, dst, n2, shift, nt, hist);
+            std::swap(src, dst);
+        }
+        FCI_CUDA(h, cudaGetLastError());
+        FCI_CUDA(h, cudaMemcpyAsync(out_addr, src, n2 * 8, cudaMemcpyDeviceToDevice, s));
+    }
+    // 4. sigma on the support
+    {
+        phase_scope ps(h, s, FCI_PHASE_SCATTER, 1);
+        k_cs_sigma<<<grid_of(n2), 256, 0, s>>>(a, out_addr, n2, out_val);
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    FCI_CUDA(h, cudaStreamSynchronize(s));
+    return FCI_OK;
+}
+
+}  // extern "C"

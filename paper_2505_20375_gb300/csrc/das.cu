@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_das_scatter(DasDev d, int64_t a0, int64
                 }
             }
         }
-        sigma[i] = first ? acc + e_core * C[i] : sigma[i] + acc;
+        sigma[i] = first ? fma(e_core, C[i], acc) : sigma[i] + acc;  // one rounding for the e_core term
     }
 }
 

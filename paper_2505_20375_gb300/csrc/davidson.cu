@@ -22,6 +22,7 @@ namespace {
 constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
 constexpr int RED_THREADS = 256;
 constexpr int KMAX = 32;
+constexpr int JAC_THREADS = 256;  // the projected eigensolver's block
 
 struct dav_scalars {      // device-resident scalars, read back each iteration
     double lam;           // lowest Ritz value (sigma carries e_core C, so e_core is included)
@@ -246,22 +247,31 @@ __global__ void k_hsub_update(double *__restrict__ Hs, const double *__restrict_
 }
 
 // Lowest eigenpair of the k x k Hermitian Hs (leading dimension KMAX, complex entries)
-// by cyclic Jacobi on the real symmetric embedding of size m = k (real) or 2k (complex).
-// Writes y (complex, k entries) and lam.  One block of 64 threads.
+// by Jacobi on the real symmetric embedding of size m = k (real) or 2k (complex), with the
+// rotations of a sweep in round-robin order: each of the M - 1 rounds (M = m rounded up to
+// even) pairs every index with one other (index M - 1 with r, and (r + i) with (r - i)
+// modulo M - 1), so the M / 2 rotations of a round touch disjoint rows and columns and run
+// at once: angles from the current A (the classical formula, tan of the angle the smaller
+// root of t^2 + 2 theta t - 1 = 0, theta = (A_qq - A_pp) / (2 A_pq)), then the columns of A
+// and Q, then the rows of A.  Sweeps stop once the off-diagonal mass is below 1e-30 of the
+// total.  Writes y (complex, k entries) and lam.  One block of JAC_THREADS threads.
 // root: 0 = lowest Ritz pair, 1 = second lowest (the real embedding of a complex Hermitian
 // matrix has every eigenvalue twice, so there the selected entry is the (2 root)-th).
-__global__ void __launch_bounds__(64) k_jacobi(const double *__restrict__ Hs, int k, int cplx, int root,
-                                               double *__restrict__ y, dav_scalars *__restrict__ out) {
+__global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const double *__restrict__ Hs, int k, int cplx, int root,
+                                                        double *__restrict__ y, dav_scalars *__restrict__ out) {
     extern __shared__ double jac_smem[];  // A and Q, each m x (m + 1)
-    __shared__ double cs[2];
+    __shared__ double cs[KMAX][2];
+    __shared__ int pr[KMAX][2];
+    __shared__ double red[2][JAC_THREADS / 32];
     __shared__ int stop;
     const int m = cplx ? 2 * k : k;
     const int ld = m + 1;
+    const int M = m + (m & 1), half = M / 2;
     double *Ab = jac_smem, *Qb = jac_smem + m * ld;
 #define A(r, c) Ab[(r) * ld + (c)]
 #define Q(r, c) Qb[(r) * ld + (c)]
-    const int t = threadIdx.x;
-    for (int i = t; i < m * m; i += blockDim.x) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    for (int i = t; i < m * m; i += nt) {
         const int r = i / m, c = i % m;
         double v;
         if (!cplx) {
@@ -275,52 +285,84 @@ __global__ void __launch_bounds__(64) k_jacobi(const double *__restrict__ Hs, in
         Q(r, c) = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
-    for (int sweep = 0; sweep < 60; ++sweep) {
+    for (int sweep = 0; sweep < 60 && m > 1; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = t; i < m * m; i += nt) {
+            const int r = i / m, c = i % m;
+            const double a2 = A(r, c) * A(r, c);
+            tot += a2;
+            if (r != c) off += a2;
+        }
+        for (int o = 16; o; o >>= 1) {
+            off += __shfl_xor_sync(0xFFFFFFFFu, off, o);
+            tot += __shfl_xor_sync(0xFFFFFFFFu, tot, o);
+        }
+        if ((t & 31) == 0) {
+            red[0][t >> 5] = off;
+            red[1][t >> 5] = tot;
+        }
+        __syncthreads();
         if (t == 0) {
-            double off = 0.0, tot = 0.0;
-            for (int r = 0; r < m; ++r)
-                for (int c = 0; c < m; ++c) {
-                    tot += A(r, c) * A(r, c);
-                    if (r != c) off += A(r, c) * A(r, c);
-                }
-            stop = (off <= 1e-30 * tot) || off == 0.0;
+            double o = 0.0, a = 0.0;
+            for (int w = 0; w < nt / 32; ++w) {
+                o += red[0][w];
+                a += red[1][w];
+            }
+            stop = (o <= 1e-30 * a) || o == 0.0;
         }
         __syncthreads();
         if (stop) break;
-        for (int p = 0; p < m - 1; ++p) {
-            for (int q = p + 1; q < m; ++q) {
+        for (int r = 0; r < M - 1; ++r) {
+            if (t < half) {
+                int p, q;
                 if (t == 0) {
+                    p = M - 1;
+                    q = r;
+                } else {
+                    p = (r + t) % (M - 1);
+                    q = (r - t + (M - 1)) % (M - 1);
+                }
+                double c = 1.0, sn = 0.0;
+                if (p < m && q < m) {
                     const double apq = A(p, q);
-                    double c = 1.0, s = 0.0;
                     if (fabs(apq) > 1e-300) {
                         const double theta = (A(q, q) - A(p, p)) / (2.0 * apq);
                         const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
                         c = 1.0 / sqrt(tt * tt + 1.0);
-                        s = tt * c;
-                    }
-                    cs[0] = c;
-                    cs[1] = s;
-                }
-                __syncthreads();
-                const double c = cs[0], s = cs[1];
-                if (s != 0.0) {
-                    if (t < m) {  // columns p, q of A and Q
-                        const double ap = A(t, p), aq = A(t, q);
-                        A(t, p) = c * ap - s * aq;
-                        A(t, q) = s * ap + c * aq;
-                        const double qp = Q(t, p), qq = Q(t, q);
-                        Q(t, p) = c * qp - s * qq;
-                        Q(t, q) = s * qp + c * qq;
-                    }
-                    __syncthreads();
-                    if (t < m) {  // rows p, q of A
-                        const double ap = A(p, t), aq = A(q, t);
-                        A(p, t) = c * ap - s * aq;
-                        A(q, t) = s * ap + c * aq;
+                        sn = tt * c;
                     }
                 }
-                __syncthreads();
+                pr[t][0] = p;
+                pr[t][1] = q;
+                cs[t][0] = c;
+                cs[t][1] = sn;
             }
+            __syncthreads();
+            for (int i = t; i < half * m; i += nt) {  // columns p, q of A and Q
+                const int j = i / m, row = i % m;
+                const double sn = cs[j][1];
+                if (sn == 0.0) continue;
+                const double c = cs[j][0];
+                const int p = pr[j][0], q = pr[j][1];
+                const double ap = A(row, p), aq = A(row, q);
+                A(row, p) = c * ap - sn * aq;
+                A(row, q) = sn * ap + c * aq;
+                const double qp = Q(row, p), qq = Q(row, q);
+                Q(row, p) = c * qp - sn * qq;
+                Q(row, q) = sn * qp + c * qq;
+            }
+            __syncthreads();
+            for (int i = t; i < half * m; i += nt) {  // rows p, q of A
+                const int j = i / m, col = i % m;
+                const double sn = cs[j][1];
+                if (sn == 0.0) continue;
+                const double c = cs[j][0];
+                const int p = pr[j][0], q = pr[j][1];
+                const double ap = A(p, col), aq = A(q, col);
+                A(p, col) = c * ap - sn * aq;
+                A(q, col) = sn * ap + c * aq;
+            }
+            __syncthreads();
         }
     }
     if (t == 0) {
@@ -579,7 +621,7 @@ struct fci_davidson_state {
             t_iter = std::chrono::steady_clock::now();
             {
                 const int m = cplx ? 2 * k : k;
-                k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, gap_phase ? 1 : 0, y,
+                k_jacobi<<<1, JAC_THREADS, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, gap_phase ? 1 : 0, y,
                                                                           scal);
             }
             FCI_CUDA(h, lincomb(V, k, y, 1.0, c, 0));
@@ -691,7 +733,7 @@ struct fci_davidson_state {
                 // c_prev / sc_prev are free in this phase and hold the ground state meanwhile
                 {
                     const int m = cplx ? 2 * k : k;
-                    k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, 0, y, scal);
+                    k_jacobi<<<1, JAC_THREADS, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, 0, y, scal);
                 }
                 FCI_CUDA(h, lincomb(V, k, y, 1.0, cp, 0));
                 FCI_CUDA(h, lincomb(S, k, y, 1.0, scp, 0));
@@ -755,7 +797,7 @@ struct fci_davidson_state {
     int finish_gap() {
         dav_scalars hs{};
         const int m = cplx ? 2 * k : k;
-        k_jacobi<<<1, 64, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, 0, y, scal);
+        k_jacobi<<<1, JAC_THREADS, 2 * m * (m + 1) * sizeof(double), s>>>(Hs, k, cplx ? 1 : 0, 0, y, scal);
         FCI_CUDA(h, lincomb(V, k, y, 1.0, c, 0));
         FCI_CUDA(h, lincomb(S, k, y, 1.0, sc, 0));
         if (cplx) k_residual<true><<<vb, RED_THREADS, 0, s>>>(c, sc, cp, false, diag, scal, n, t, partial);

@@ -576,13 +576,15 @@ static int check_opts(fci_context *h, const fci_davidson_opts *o) {
         return fci_fail(h, FCI_ERR_ARG, "unknown final precision %d", o->final_precision);
     if (o->final_precision == FCI_PREC_OZ_BF16 && (o->final_slices < 6 || o->final_slices > 8))
         return fci_fail(h, FCI_ERR_ARG, "final_slices %d outside [6, 8]", o->final_slices);
-    if (h->das_active) {  // the DAS split path takes 2 or 3 slices; its FP64-class phase is FP64
+    if (h->das_active) {  // the DAS split forms: 2 or 3 slices fused, 4 and more two-pass
         if (o->precision == FCI_PREC_OZ_BF16) {
-            const int rc = dz_check(h, o->n_slices);
+            const int rc = das_split_check(h, o->n_slices);
             if (rc) return rc;
         }
-        if (o->final_precision == FCI_PREC_OZ_BF16)
-            return fci_fail(h, FCI_ERR_UNSUPPORTED, "DAS layout: the final phase runs in FCI_PREC_FP64");
+        if (o->final_precision == FCI_PREC_OZ_BF16) {
+            const int rc = das_split_check(h, o->final_slices);
+            if (rc) return rc;
+        }
     }
     return FCI_OK;
 }
@@ -675,6 +677,8 @@ int fci_tune_sigma(fci_handle h, int n_slices, const void *C, void *sigma, void 
     cudaStream_t s = (cudaStream_t)stream;
     int a[8] = {0}, b[8] = {0}, n = 0;
     if (h->das_active) {
+        if (n_slices >= 4)
+            return fci_fail(h, FCI_ERR_UNSUPPORTED, "the DAS two-pass split form (%d slices) has no tile choice", n_slices);
         if ((rc = dz_check(h, n_slices))) return rc;
         n = dz_tune_candidates(h, n_slices, a, b, 8);
     } else {
@@ -783,14 +787,15 @@ int fci_sigma_grouped(const fci_sigma_job *jobs, int n_jobs, fci_stream stream) 
     // split-precision DAS jobs, grouped by slice count
     for (int i = 0; i < n_jobs; ++i) {
         const fci_sigma_job &j = jobs[i];
-        if (done[i] || j.precision != FCI_PREC_OZ_BF16 || !j.handle->das_active) continue;
+        if (done[i] || j.precision != FCI_PREC_OZ_BF16 || !j.handle->das_active || j.n_slices > 3) continue;
         std::vector<fci_context *> hs;
         std::vector<const double *> Cs;
         std::vector<double *> ss;
         std::vector<void *> ws;
         for (int k = i; k < n_jobs; ++k) {
             const fci_sigma_job &q = jobs[k];
-            if (done[k] || q.precision != FCI_PREC_OZ_BF16 || q.n_slices != j.n_slices || !q.handle->das_active)
+            if (done[k] || q.precision != FCI_PREC_OZ_BF16 || q.n_slices != j.n_slices || !q.handle->das_active ||
+                q.n_slices > 3)
                 continue;
             hs.push_back(q.handle);
             Cs.push_back((const double *)q.C);

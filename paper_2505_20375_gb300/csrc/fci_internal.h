@@ -66,6 +66,9 @@ struct fci_das_layout {
     int32_t *d_dz_base = nullptr;  // [target | intermediate block offset per pattern pair (-1: none) | n_str_b]
     void *d_dz_G = nullptr;
     int dz_slices = 0, dz_shG = 0;
+    // the two-pass form (s >= 4): G digit slices in the A-tile layout of the bulk-copy GEMM
+    void *d_dg_G = nullptr;
+    int dg_slices = 0, dg_shG = 0;
     // kernel configuration chosen by the tuner for dz_tuned_slices (0: none)
     int dz_tuned_slices = 0, dz_tuned_kch = 0, dz_tuned_pw = 0;
 };
@@ -211,6 +214,10 @@ void dz_free(fci_das_layout &L);
 int dz_tune_candidates(const fci_context *h, int n_slices, int *kch, int *pw, int max);  // fitting configurations
 void dz_set_config(fci_context *h, int n_slices, int kch, int pw);                     // kch = 0: default
 int dz_check(fci_context *h, int n_slices);  // FCI_OK if the DAS split path takes this problem
+int das_split_check(fci_context *h, int n_slices);  // either DAS split form (s <= 3 fused, s >= 4 two-pass)
+int dg_check(fci_context *h, int n_slices);         // the DAS two-pass split form (s = 4 .. 8)
+size_t dg_workspace_bytes(const fci_context *h, int n_slices);
+int dg_sigma(fci_context *h, const double *C, double *sigma, int n_slices, void *ws, cudaStream_t s);
 
 // ozaki_cplx.cu (spinor strings, complex integrals)
 int cz_check(fci_context *h, int n_slices);
@@ -218,6 +225,8 @@ size_t cz_workspace_bytes(const fci_context *h, int n_slices);
 int cz_sigma(fci_context *h, const double *C, double *sigma, int n_slices, void *ws, size_t ws_bytes, cudaStream_t s);
 
 // ozaki.cu
+cudaError_t launch_to_fixed64(const double *C, int64_t n, int s, unsigned long long *maxbits, int64_t *Cint, int *shC,
+                              cudaStream_t st);
 int oz_prepare_G(fci_context *h, int n_slices);
 int oz_tune_candidates(const fci_context *h, int n_slices, int *nt, int *path, int max);  // configurations that fit
 void oz_set_config(fci_context *h, int n_slices, int nt, int path);                     // nt = 0: default

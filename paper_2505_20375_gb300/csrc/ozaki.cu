@@ -582,6 +582,16 @@ int oz_nt(const fci_context *h, int s) {
 
 }  // namespace
 
+// Fixed point of C for the split paths with int64 digits: maxbits (zeroed by the caller)
+// receives the largest |C| bit pattern, shC the shift, Cint = round(C 2^{sh_C}).
+cudaError_t launch_to_fixed64(const double *C, int64_t n, int s, unsigned long long *maxbits, int64_t *Cint, int *shC,
+                              cudaStream_t st) {
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 8));
+    k_absmax_bits<<<nb, 256, 0, st>>>(C, n, maxbits);
+    k_to_fixed<<<nb, 256, 0, st>>>(C, n, s, maxbits, Cint, shC);
+    return cudaGetLastError();
+}
+
 // IEEE binary16 encoding of an integer |d| <= 1024 (exact).
 static uint16_t half_bits_of_small_int(int d) {
     if (d == 0) return 0;

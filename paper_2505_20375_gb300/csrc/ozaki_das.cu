@@ -45,6 +45,7 @@
 #include <vector>
 
 #include "das_dev.cuh"
+#include "oz_gemm.cuh"
 #include "tc_ptx.cuh"
 
 namespace {
@@ -503,10 +504,10 @@ struct DzScatter {
     const int32_t *nstr_b32;
     const int64_t *cat_off, *locbase_a, *locbase_b;
     const int32_t *cat_pa, *cat_pb;
-    const float *E;
+    const void *E;  // FP32 [tile of 128][n_pair][128] (fused form) or int64 [tile of 64][n_pair][64] (two-pass)
     const double *C;
     double e_core;
-    int ushift;  // 8 (s - 1) - sh_G; the scale is 2^(ushift - sh_C)
+    int ushift;  // 8 L0 - sh_G (L0 = s - 1 in the fused form); the scale is 2^(ushift - sh_C)
     const int *shC, *status;
     int *sticky;  // the handle's status word (fci_sync_status)
     int mode;    // 0: single chunk (write sigma); 1: first of several; 2: middle; 3: last
@@ -519,6 +520,9 @@ struct DzScatter {
 // determinants; when they share the alpha string, lanes 0-7 resolve the alpha moves of 8
 // pairs at a time and broadcast them (alpha targets are 32 consecutive K), and beta
 // targets use a per-warp table of row offsets.  Loads are issued 16 at a time.
+// ET, LOG2T: the element type of E and the log2 of its tile width (FP32 holding an
+// integer and 128 for the fused kernel, int64 and 64 for the two-pass GEMM).
+template <typename ET, int LOG2T>
 __global__ void __launch_bounds__(256) k_dz_scatter(const __grid_constant__ DzScatter a) {
     extern __shared__ int32_t sc_tab[];
     const int npb = a.n_pat_b, npab = a.n_pat_a * npb;
@@ -531,7 +535,9 @@ __global__ void __launch_bounds__(256) k_dz_scatter(const __grid_constant__ DzSc
     const int u = a.ushift - *a.shC;
     const bool bad = *a.status != 0;
     if (bad && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(a.sticky, *a.status);  // kept for fci_sync_status
-    const int64_t tstride = (int64_t)a.npair * DZ_TILE;
+    constexpr int32_t TMASK = (1 << LOG2T) - 1;
+    const ET *E = (const ET *)a.E;
+    const int64_t tstride = (int64_t)a.npair << LOG2T;
     const int32_t len = (int32_t)a.len, a0 = (int32_t)a.a0;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t wbase = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; wbase < a.n_det;
@@ -599,17 +605,24 @@ __global__ void __launch_bounds__(256) k_dz_scatter(const __grid_constant__ DzSc
                     sgn |= ((uint32_t)(ea & 1) << e) | ((uint32_t)(eb & 1) << (8 + e));
                 }
             }
-            float va[8], vb[8];
+            ET va[8], vb[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const bool oa = live && Ka[e] >= 0 && Ka[e] < len, ob = Kb[e] >= 0 && Kb[e] < len;
                 const int32_t ka = oa ? Ka[e] : 0, kb = ob ? Kb[e] : 0;
-                va[e] = oa ? __ldg(a.E + (int64_t)(ka >> 7) * tstride + (p0 + e) * DZ_TILE + (ka & 127)) : 0.f;
-                vb[e] = ob ? __ldg(a.E + (int64_t)(kb >> 7) * tstride + (p0 + e) * DZ_TILE + (kb & 127)) : 0.f;
+                va[e] = oa ? __ldg(E + (int64_t)(ka >> LOG2T) * tstride + ((p0 + e) << LOG2T) + (ka & TMASK)) : (ET)0;
+                vb[e] = ob ? __ldg(E + (int64_t)(kb >> LOG2T) * tstride + ((p0 + e) << LOG2T) + (kb & TMASK)) : (ET)0;
             }
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int64_t xa = __float2ll_rn(va[e]), xb = __float2ll_rn(vb[e]);
+                int64_t xa, xb;
+                if constexpr (sizeof(ET) == 4) {
+                    xa = __float2ll_rn(va[e]);
+                    xb = __float2ll_rn(vb[e]);
+                } else {
+                    xa = va[e];
+                    xb = vb[e];
+                }
                 acc += (((sgn >> e) & 1) ? -xa : xa) + (((sgn >> (8 + e)) & 1) ? -xb : xb);
             }
         }
@@ -724,12 +737,10 @@ int dz_check(fci_context *h, int s) {
 
 namespace {
 
-// G digit slices (B operand: N = pair rows pq, K = pair columns rs, canonical K-major
-// core matrices), the packed replacement tables and the block-offset table.
-int dz_prepare(fci_context *h, int s, cudaStream_t st) {
+// The packed replacement tables and the block-offset table (both split forms).
+int dz_prepare_tables(fci_context *h, cudaStream_t st) {
     fci_das_layout &L = h->das;
-    int rc = dz_check(h, s);
-    if (rc) return rc;
+    int rc = FCI_OK;
     if (!L.d_dz_rep_a) {
         const int Np = h->npair_pad;
         const int64_t nla = dz_nloc(L.pat_nstr_a), nlb = dz_nloc(L.pat_nstr_b);
@@ -753,6 +764,16 @@ int dz_prepare(fci_context *h, int s, cudaStream_t st) {
         for (int b = 0; b < L.n_pat_b; ++b) tb[2 * npab + b] = (int32_t)L.pat_nstr_b[b];
         FCI_CUDA(h, cudaMemcpy(L.d_dz_base, tb.data(), tb.size() * 4, cudaMemcpyHostToDevice));
     }
+    return rc;
+}
+
+// G digit slices (B operand: N = pair rows pq, K = pair columns rs, canonical K-major
+// core matrices), the packed replacement tables and the block-offset table.
+int dz_prepare(fci_context *h, int s, cudaStream_t st) {
+    fci_das_layout &L = h->das;
+    int rc = dz_check(h, s);
+    if (!rc) rc = dz_prepare_tables(h, st);
+    if (rc) return rc;
     if (L.dz_slices != s || !L.d_dz_G) {
         const int np = h->npair, Np = h->npair_pad, KC = Np / 8;
         std::vector<double> G((size_t)np * np);
@@ -947,10 +968,11 @@ int dz_scatter(const DzJob &j, int s, int chunk, cudaStream_t st) {
     a.acc = j.acc;
     a.sigma = j.sigma;
     const size_t smem = dz_scatter_table_bytes(L);
-    if (smem > 48 * 1024) FCI_CUDA(h, cudaFuncSetAttribute(k_dz_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024)
+        FCI_CUDA(h, cudaFuncSetAttribute(k_dz_scatter<float, 7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
     const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.n_det, 256), 152 * 8));
-    k_dz_scatter<<<nb, 256, smem, st>>>(a);
+    k_dz_scatter<float, 7><<<nb, 256, smem, st>>>(a);
     FCI_CUDA(h, cudaGetLastError());
     return FCI_OK;
 }
@@ -962,19 +984,340 @@ int dz_num_sms(fci_context *h, int *nsm) {
 
 }  // namespace
 
+// ------------------------------------------------------- two-pass form (s = 4 .. 8)
+//
+// For an FP64-class split (6 or 7 slices) the s level accumulators of the fused form do not
+// fit in TMEM, and neither do its G slices in shared memory, so the contraction turns back
+// to the orientation of the alpha/beta two-pass path: pair rows on M (ceil(n_pair / 128)
+// M-tiles of G digits), 64 determinants on N, and the operands streamed from HBM:
+//   k_dg_split   writes the digit image of D (int64 fixed point of C, gathered through the
+//                packed replacement tables and the target block offsets) for a piece of
+//                the intermediate space, in the B-tile layout of the bulk-copy GEMM;
+//   k_oz_gemm    (8-bit digits, K-chunks of 32) sums the top s levels exactly in TMEM and
+//                stores E_int (int64) [tile of 64][n_pair][64];
+//   k_dz_scatter (int64 form) sums E_int exactly per target determinant.
+// Every level sum stays an integer below 2^24 when s n_pair <= 1023 (n_pair nonzero terms
+// of products below 2^14, s products per level), which the check enforces.  E covers up to
+// a cap of the intermediate space at a time (the scatter runs once per E chunk); the digit
+// image covers a smaller piece of that chunk at a time.
+namespace {
+
+constexpr int DG_KCC = 4;                      // core matrices (8 pairs) per K-chunk of the GEMM
+constexpr int DG_KW = 8 * DG_KCC;              // 32 pairs per K-chunk
+constexpr int DG_B_PLANE = OZG_N * DG_KW * 2;  // 4 KB: 64 determinants x 32 pairs, f16
+constexpr int DG_A_PLANE = OZG_M * DG_KW * 2;  // 8 KB: 128 pair rows x 32 pairs, f16
+
+struct DgGeom {
+    int n_mt, n_kc;        // M-tiles of 128 pair rows; K-chunks of 32 pairs
+    int64_t e_cap, d_cap;  // determinants per E chunk and per digit-image piece (multiples of 64)
+    int n_echunks;
+};
+
+// FCI_DAS_CHUNK_DETS and FCI_DAS_IMAGE_DETS lower the two caps (in determinants) so that
+// tests can force several chunks and pieces on small problems.
+DgGeom dg_geom(const fci_context *h, int s) {
+    const fci_das_layout &L = h->das;
+    DgGeom g;
+    g.n_mt = (h->npair + OZG_M - 1) / OZG_M;
+    g.n_kc = (h->npair_pad + DG_KW - 1) / DG_KW;
+    const int64_t all = ceil_div(std::max<int64_t>(L.n_det_int, 1), OZG_N) * OZG_N;
+    int64_t e = (((int64_t)96 << 30) / (8 * (int64_t)h->npair)) / OZG_N * OZG_N;
+    if (const char *env = getenv("FCI_DAS_CHUNK_DETS"))
+        if (atoll(env) > 0) e = ceil_div(atoll(env), OZG_N) * OZG_N;
+    g.e_cap = std::max<int64_t>(OZG_N, std::min(e, all));
+    int64_t d = (((int64_t)24 << 30) / ((int64_t)g.n_kc * s * DG_B_PLANE / OZG_N)) / OZG_N * OZG_N;
+    if (const char *env = getenv("FCI_DAS_IMAGE_DETS"))
+        if (atoll(env) > 0) d = ceil_div(atoll(env), OZG_N) * OZG_N;
+    g.d_cap = std::max<int64_t>(OZG_N, std::min(d, g.e_cap));
+    g.n_echunks = (int)ceil_div(all, g.e_cap);
+    return g;
+}
+
+struct DgSplit {
+    int64_t a0, len;   // intermediate addresses [a0, a0 + len) of this piece
+    int64_t n_nt;      // tiles of 64
+    int n_kc, npair_pad, n_cat_int, n_pat_b;
+    int64_t nla, nlb;
+    const int32_t *repA, *repB;
+    const int32_t *base_tgt;  // [n_pat_a * n_pat_b]: offset of a TARGET block, else -1 (C is zero)
+    const int32_t *nstr_b32;
+    const int64_t *cat_off, *locbase_a, *locbase_b;
+    const int32_t *cat_pa, *cat_pb;
+    const int64_t *Cint;
+    uint8_t *Dimg;
+};
+
+// Digit image of D for one piece: tile nt (64 determinants) holds, per K-chunk of 32
+// pairs, S f16 planes of 64 x 32 in canonical K-major core matrices.  Thread t covers
+// determinant t % 64 of the tile (decoded once: category, patterns, local indices) and
+// pairs 8 (t / 64) .. 8 (t / 64) + 7 of every chunk; D_int of a pair is the alpha move's
+// and the beta move's signed C_int (zero where the move leaves the target space or does
+// not exist; replacement-table rows past n_pair_pad count as absent).
+template <int S>
+__global__ void __launch_bounds__(64 * DG_KCC) k_dg_split(const __grid_constant__ DgSplit a) {
+    constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
+    const int row = threadIdx.x & 63, cc = threadIdx.x >> 6;
+    const int npb = a.n_pat_b;
+    for (int64_t nt = blockIdx.x; nt < a.n_nt; nt += gridDim.x) {
+        const int64_t off = nt * OZG_N + row;
+        const bool live = off < a.len;
+        int32_t pa = 0, pb = 0, la = 0, lb = 0, nb = 1;
+        int64_t ida = 0, idb = 0;
+        if (live) {
+            const int64_t addr = a.a0 + off;
+            const int c = find_cat(a.cat_off, a.n_cat_int, addr);
+            pa = __ldg(a.cat_pa + c);
+            pb = __ldg(a.cat_pb + c);
+            nb = __ldg(a.nstr_b32 + pb);
+            const int32_t rr = (int32_t)(addr - __ldg(a.cat_off + c));
+            la = rr / nb;
+            lb = rr - la * nb;
+            ida = __ldg(a.locbase_a + pa) + la;
+            idb = __ldg(a.locbase_b + pb) + lb;
+        }
+        uint8_t *tile = a.Dimg + (size_t)nt * a.n_kc * S * DG_B_PLANE + ((row >> 3) * DG_KCC + cc) * 128 + (row & 7) * 16;
+#pragma unroll 1
+        for (int kc = 0; kc < a.n_kc; ++kc) {
+            const int rs0 = kc * DG_KW + cc * 8;
+            int32_t ea[8], eb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const bool ok = live && rs0 + e < a.npair_pad;
+                ea[e] = ok ? __ldg(a.repA + (int64_t)(rs0 + e) * a.nla + ida) : -1;
+                eb[e] = ok ? __ldg(a.repB + (int64_t)(rs0 + e) * a.nlb + idb) : -1;
+            }
+            int32_t Ka[8], Kb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int32_t ba = ea[e] >= 0 ? __ldg(a.base_tgt + (ea[e] >> 23) * npb + pb) : -1;
+                const int32_t bb = eb[e] >= 0 ? __ldg(a.base_tgt + pa * npb + (eb[e] >> 23)) : -1;
+                Ka[e] = ba >= 0 ? ba + ((ea[e] >> 1) & DZ_LOC_MASK) * nb + lb : -1;
+                Kb[e] = bb >= 0 ? bb + la * __ldg(a.nstr_b32 + (eb[e] >> 23)) + ((eb[e] >> 1) & DZ_LOC_MASK) : -1;
+            }
+            uint32_t ylo[8], yhi[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int64_t xa = Ka[e] >= 0 ? __ldg(a.Cint + Ka[e]) : 0;
+                const int64_t xb = Kb[e] >= 0 ? __ldg(a.Cint + Kb[e]) : 0;
+                const int64_t v = ((ea[e] & 1) ? -xa : xa) + ((eb[e] & 1) ? -xb : xb);
+                const uint64_t y = (uint64_t)v + bias;
+                ylo[e] = (uint32_t)y;
+                yhi[e] = (uint32_t)(y >> 32);
+            }
+            uint8_t *base = tile + (size_t)kc * S * DG_B_PLANE;
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                const uint32_t bj = (uint32_t)(j & 3), sel = bj | ((4u + bj) << 8);
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2)
+                    w[e / 2] = j < 4 ? digits_f16x2(ylo[e], ylo[e + 1], sel) : digits_f16x2(yhi[e], yhi[e + 1], sel);
+                __stcs((uint4 *)(base + j * DG_B_PLANE), make_uint4(w[0], w[1], w[2], w[3]));
+            }
+        }
+    }
+}
+
+// G digit slices in the A-tile layout of the bulk-copy GEMM: [M-tile][K-chunk][plane][128 x 32].
+int dg_prepare_G(fci_context *h, int s) {
+    fci_das_layout &L = h->das;
+    if (L.dg_slices == s && L.d_dg_G) return FCI_OK;
+    const DgGeom g = dg_geom(h, s);
+    const int np = h->npair;
+    std::vector<double> G((size_t)np * np);
+    if (cudaMemcpy(G.data(), h->d_G, G.size() * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fci_cuda_check(h, cudaGetLastError(), "G download");
+    double gmax = 0.0;
+    for (double v : G) gmax = std::max(gmax, fabs(v));
+    int eG = 0;
+    if (gmax > 0) frexp(gmax, &eG);  // gmax < 2^eG
+    const int shG = 8 * s - 2 - eG;
+    const uint64_t bias = 0x8080808080808080ull >> (8 * (8 - s));
+    const size_t stage = (size_t)s * DG_A_PLANE;
+    std::vector<uint16_t> img((size_t)g.n_mt * g.n_kc * stage / 2, 0);
+    for (int m = 0; m < g.n_mt * OZG_M; ++m)
+        for (int k = 0; k < g.n_kc * DG_KW; ++k) {
+            int64_t gi = 0;
+            if (m < np && k < np) gi = llrint(ldexp(G[(size_t)m * np + k], shG));
+            const uint64_t y = (uint64_t)gi + bias;
+            const int mt = m / OZG_M, mm = m % OZG_M, kc = k / DG_KW, kk = k % DG_KW;
+            const size_t off = ((size_t)mt * g.n_kc + kc) * stage + ((mm >> 3) * DG_KCC + (kk >> 3)) * 128 + (mm & 7) * 16 +
+                               (kk & 7) * 2;
+            for (int j = 0; j < s; ++j)
+                img[(off + (size_t)j * DG_A_PLANE) / 2] = half_bits_of_small_int((int)((y >> (8 * j)) & 0xFF) - 128);
+        }
+    fci_dev_free(L.d_dg_G);
+    L.d_dg_G = nullptr;
+    L.dg_slices = 0;
+    int rc = fci_dev_alloc(h, &L.d_dg_G, img.size() * 2);
+    if (rc) return rc;
+    FCI_CUDA(h, cudaMemcpy(L.d_dg_G, img.data(), img.size() * 2, cudaMemcpyHostToDevice));
+    L.dg_slices = s;
+    L.dg_shG = shG;
+    return FCI_OK;
+}
+
+}  // namespace
+
+int dg_check(fci_context *h, int s) {
+    const fci_das_layout &L = h->das;
+    if (h->dtype != FCI_R64) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision is built for real integrals");
+    if (s < 4 || s > 8) return fci_fail(h, FCI_ERR_UNSUPPORTED, "the DAS two-pass split takes 4 to 8 slices");
+    if (s * h->npair > 1023)
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices x %d pairs: level sums could exceed 2^24", s, h->npair);
+    if (L.n_pat_a > 256 || L.n_pat_b > 256) return fci_fail(h, FCI_ERR_UNSUPPORTED, "more than 256 patterns per spin");
+    if (L.n_det_int >= ((int64_t)1 << 30))
+        return fci_fail(h, FCI_ERR_UNSUPPORTED, "the split path takes < 2^30 intermediate determinants");
+    for (int64_t v : L.pat_nstr_a)
+        if (v > DZ_LOC_MASK) return fci_fail(h, FCI_ERR_UNSUPPORTED, "a pattern has more than 2^22 strings");
+    for (int64_t v : L.pat_nstr_b)
+        if (v > DZ_LOC_MASK) return fci_fail(h, FCI_ERR_UNSUPPORTED, "a pattern has more than 2^22 strings");
+    if (!oz_gemm_ring(s, DG_KCC, 0)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "%d slices do not fit the GEMM pipeline", s);
+    return FCI_OK;
+}
+
+int das_split_check(fci_context *h, int s) { return s <= 3 ? dz_check(h, s) : dg_check(h, s); }
+
+size_t dg_workspace_bytes(const fci_context *h, int s) {
+    const DgGeom g = dg_geom(h, std::max(s, 4));
+    size_t b = al256((size_t)h->das.n_det * 8) + al256((size_t)(g.d_cap / OZG_N) * g.n_kc * std::max(s, 4) * DG_B_PLANE) +
+               al256((size_t)g.e_cap * h->npair * 8);
+    if (g.n_echunks > 1) b += al256((size_t)h->das.n_det * 8);
+    return b + 256;
+}
+
+int dg_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, cudaStream_t st) {
+    int rc = dg_check(h, s);
+    if (!rc) rc = dz_prepare_tables(h, st);
+    if (!rc) rc = dg_prepare_G(h, s);
+    if (rc) return rc;
+    const fci_das_layout &L = h->das;
+    const DgGeom g = dg_geom(h, s);
+    char *p = (char *)ws;
+    int64_t *Cint = (int64_t *)p;
+    p += al256((size_t)L.n_det * 8);
+    uint8_t *Dimg = (uint8_t *)p;
+    p += al256((size_t)(g.d_cap / OZG_N) * g.n_kc * s * DG_B_PLANE);
+    int64_t *E = (int64_t *)p;
+    p += al256((size_t)g.e_cap * h->npair * 8);
+    int64_t *acc = nullptr;
+    if (g.n_echunks > 1) {
+        acc = (int64_t *)p;
+        p += al256((size_t)L.n_det * 8);
+    }
+    unsigned long long *maxbits = (unsigned long long *)p;
+    int *shC = (int *)(p + 8), *status = (int *)(p + 16);
+    {
+        phase_scope ps(h, st, FCI_PHASE_OTHER, 2);
+        FCI_CUDA(h, cudaMemsetAsync(p, 0, 256, st));
+        FCI_CUDA(h, launch_to_fixed64(C, L.n_det, s, maxbits, Cint, shC, st));
+    }
+    const size_t npab = (size_t)L.n_pat_a * L.n_pat_b;
+    DgSplit sp;
+    sp.n_kc = g.n_kc;
+    sp.npair_pad = h->npair_pad;
+    sp.n_cat_int = L.n_cat_int;
+    sp.n_pat_b = L.n_pat_b;
+    sp.nla = dz_nloc(L.pat_nstr_a);
+    sp.nlb = dz_nloc(L.pat_nstr_b);
+    sp.repA = L.d_dz_rep_a;
+    sp.repB = L.d_dz_rep_b;
+    sp.base_tgt = L.d_dz_base;
+    sp.nstr_b32 = L.d_dz_base + 2 * npab;
+    sp.cat_off = L.d_cat_off;
+    sp.locbase_a = L.d_pat_locbase_a;
+    sp.locbase_b = L.d_pat_locbase_b;
+    sp.cat_pa = L.d_cat_pa;
+    sp.cat_pb = L.d_cat_pb;
+    sp.Cint = Cint;
+    sp.Dimg = Dimg;
+    for (int ec = 0; ec < g.n_echunks; ++ec) {
+        const int64_t e0 = (int64_t)ec * g.e_cap, elen = std::min(g.e_cap, L.n_det_int - e0);
+        for (int64_t d0 = 0; d0 < elen; d0 += g.d_cap) {
+            sp.a0 = e0 + d0;
+            sp.len = std::min(g.d_cap, elen - d0);
+            sp.n_nt = ceil_div(sp.len, OZG_N);
+            {
+                phase_scope ps(h, st, FCI_PHASE_GATHER, 1);
+                const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(sp.n_nt, 152 * 16));
+                switch (s) {
+                    case 4: k_dg_split<4><<<gb, 64 * DG_KCC, 0, st>>>(sp); break;
+                    case 5: k_dg_split<5><<<gb, 64 * DG_KCC, 0, st>>>(sp); break;
+                    case 6: k_dg_split<6><<<gb, 64 * DG_KCC, 0, st>>>(sp); break;
+                    case 7: k_dg_split<7><<<gb, 64 * DG_KCC, 0, st>>>(sp); break;
+                    default: k_dg_split<8><<<gb, 64 * DG_KCC, 0, st>>>(sp); break;
+                }
+                FCI_CUDA(h, cudaGetLastError());
+            }
+            oz_gemm_args a;
+            a.n_mt = g.n_mt;
+            a.n_kc = g.n_kc;
+            a.M_pad = h->npair;  // E row stride: the n_pair rows of each tile, no padding
+            a.M_real = h->npair;
+            a.n_nt = sp.n_nt;
+            a.Gimg = L.d_dg_G;
+            a.Dimg = Dimg;
+            a.E = E + (size_t)(d0 / OZG_N) * h->npair * OZG_N;
+            a.status = status;
+            if ((rc = oz_gemm_launch(h, s, 8, DG_KCC, false, a, st))) return rc;
+        }
+        DzScatter sc;
+        sc.n_det = L.n_det;
+        sc.nla = (int)sp.nla;
+        sc.nlb = (int)sp.nlb;
+        sc.a0 = e0;
+        sc.len = elen;
+        sc.n_cat = L.n_cat;
+        sc.n_pat_a = L.n_pat_a;
+        sc.n_pat_b = L.n_pat_b;
+        sc.npair = h->npair;
+        sc.repA = L.d_dz_rep_a;
+        sc.repB = L.d_dz_rep_b;
+        sc.base_int = L.d_dz_base + npab;
+        sc.nstr_b32 = L.d_dz_base + 2 * npab;
+        sc.cat_off = L.d_cat_off;
+        sc.locbase_a = L.d_pat_locbase_a;
+        sc.locbase_b = L.d_pat_locbase_b;
+        sc.cat_pa = L.d_cat_pa;
+        sc.cat_pb = L.d_cat_pb;
+        sc.E = E;
+        sc.C = C;
+        sc.e_core = h->e_core;
+        sc.ushift = 8 * oz_gemm_L0(s, 8) - L.dg_shG;
+        sc.shC = shC;
+        sc.status = status;
+        sc.sticky = h->d_status;
+        sc.mode = g.n_echunks == 1 ? 0 : ec == 0 ? 1 : ec == g.n_echunks - 1 ? 3 : 2;
+        sc.acc = acc;
+        sc.sigma = sigma;
+        const size_t smem = dz_scatter_table_bytes(L);
+        if (smem > 48 * 1024)
+            FCI_CUDA(h, cudaFuncSetAttribute(k_dz_scatter<int64_t, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+        phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
+        const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.n_det, 256), 152 * 8));
+        k_dz_scatter<int64_t, 6><<<nb, 256, smem, st>>>(sc);
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    return FCI_OK;
+}
+
 void dz_free(fci_das_layout &L) {
     fci_dev_free(L.d_dz_rep_a);
     fci_dev_free(L.d_dz_rep_b);
     fci_dev_free(L.d_dz_base);
     fci_dev_free(L.d_dz_G);
+    fci_dev_free(L.d_dg_G);
     L.d_dz_rep_a = L.d_dz_rep_b = nullptr;
     L.d_dz_base = nullptr;
     L.d_dz_G = nullptr;
+    L.d_dg_G = nullptr;
     L.dz_slices = 0;
+    L.dg_slices = 0;
 }
 
 size_t dz_workspace_bytes(const fci_context *h, int s) {
-    (void)s;
+    if (s >= 4) return dg_workspace_bytes(h, s);
     std::vector<std::pair<int, int>> ch;
     int64_t max_len = 0;
     dz_chunks(h, ch, max_len);
@@ -984,6 +1327,7 @@ size_t dz_workspace_bytes(const fci_context *h, int s) {
 }
 
 int dz_sigma(fci_context *h, const double *C, double *sigma, int s, void *ws, size_t ws_bytes, cudaStream_t st) {
+    if (s >= 4) return dg_sigma(h, C, sigma, s, ws, st);
     (void)ws_bytes;
     DzJob j;
     int rc = dz_prepare_job(h, C, sigma, s, ws, st, j);

@@ -1,9 +1,13 @@
-// Kernel layout (one persistent CTA per SM, 320 or 576 threads):
+// Kernel layout (one persistent CTA per SM, 352 or 608 threads):
 //   warp 0     lane 0 issues the two bulk copies of each pipeline stage (A tile: s planes
 //              of 128 x 32, B tile: s planes of 64 x 32), completing on the stage's mbarrier;
-//   warp 1     allocates TMEM; lane 0 issues the MMAs (M = 128, N = 64, K = 16) into the
-//              s level accumulators and commits;
-//   warps 2..  epilogue: 8 warps (two per TMEM lane quadrant, 32 columns each) when the
+//   warps 1, 2 lane 0 of each issues the MMAs (M = 128, N = 64, K = 16) of half of the s
+//              level accumulators and commits (warp 1 also allocates TMEM): two issuing
+//              threads on two SM sub-partitions, because one thread issuing every MMA was
+//              measured at about 77 cycles per MMA against 48 for the bare instruction
+//              stream; the levels are dealt so that both issue about as many MMAs
+//              (level l, which takes s - l products, to issuer ((l + 1) / 2) mod 2);
+//   warps 3..  epilogue: 8 warps (two per TMEM lane quadrant, 32 columns each) when the
 //              accumulators are double-buffered (s <= 4), else 16 (four per quadrant,
 //              16 columns each), which read the levels three at a time and release each
 //              group as soon as it is in registers.
@@ -18,6 +22,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "oz_gemm.cuh"
 #include "tc_ptx.cuh"
@@ -29,7 +34,10 @@ using namespace tc;
 // Epilogue warps: 8 (two per TMEM lane quadrant, 32 columns each) when the level
 // accumulators are double-buffered, 16 (four per quadrant, 16 columns each) otherwise.
 __host__ __device__ constexpr int ozg_epi_warps(int s) { return 2 * s * OZG_N <= 512 ? 8 : 16; }
-__host__ __device__ constexpr int ozg_threads(int s) { return 32 * (2 + ozg_epi_warps(s)); }
+__host__ __device__ constexpr int ozg_threads(int s) { return 32 * (3 + ozg_epi_warps(s)); }
+constexpr int OZG_ISSUERS = 2;
+// The MMA issuer of level l (0 = the lowest kept level, which takes the most products).
+__host__ __device__ constexpr int ozg_issuer(int l) { return ((l + 1) >> 1) & 1; }
 constexpr int OZG_MAX_STAGES = 6;
 constexpr size_t OZG_SMEM_MAX = 232448 - 1024;
 
@@ -127,11 +135,11 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
     if (threadIdx.x == 0) {
         for (int r = 0; r < R; ++r) {
             mbar_init(smem_u32(&sh->full[r]), 1);
-            mbar_init(smem_u32(&sh->empty[r]), 1);
+            mbar_init(smem_u32(&sh->empty[r]), OZG_ISSUERS);  // both issuers' MMAs of the stage done
         }
-        for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&sh->acc_full[b]), 1);
+        for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&sh->acc_full[b]), OZG_ISSUERS);
         for (int b = 0; b < 3; ++b) mbar_init(smem_u32(&sh->acc_empty[b]), ozg_epi_warps(S));
-        mbar_init(smem_u32(&sh->drain), 1);
+        mbar_init(smem_u32(&sh->drain), OZG_ISSUERS);
         mbar_init(smem_u32(&sh->a_full), 1);
         sh->abort = 0;
         fence_barrier_init();
@@ -191,9 +199,12 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
             }
             if (RESA) ozg_drain_wait(smem_u32(&sh->a_full), 0, p.status, p.timeout_cycles);
         }
-    } else if (warp == 1) {
-        if (lane == 0) {
-            // ------------------------------------------------------------ MMA issuer
+    } else if (warp <= OZG_ISSUERS) {
+        // ---------------------------------------------------------------- MMA issuers
+        // ME (a compile-time copy of warp - 1): this thread issues the levels l with
+        // ozg_issuer(l) == ME, so each issuer's instruction stream holds its MMAs only.
+        auto issuer = [&](auto me_c) {
+            constexpr int ME = decltype(me_c)::value;
             // The ring slot and its parity advance with each stage (no division on the
             // issue path), and each wait first tests the barrier without blocking.
             auto wait = [&](uint32_t bar, uint32_t par) -> bool {
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
 #pragma unroll
                                 for (int i = S - 1 - j; i < S; ++i) {
                                     const int lv = i + j - (S - 1);
-                                    if (lv >= lo && lv < hi)
+                                    if (lv >= lo && lv < hi && ozg_issuer(lv) == ME)
                                         mma_f16(dbase + (uint32_t)(lv * OZG_N),
                                                 as + (uint64_t)((i * A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
                                 }
@@ -266,14 +277,18 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
                 if (!ok) break;
                 mma_commit(smem_u32(&sh->acc_full[buf]));
             }
-            if (issued) {
-                // all MMAs issued must complete before TMEM is freed; if the first budget
-                // expires (FCI_ERR_TIMEOUT recorded) a second one follows before the
-                // deallocation goes ahead
-                mma_commit(smem_u32(&sh->drain));
-                if (!ozg_drain_wait(smem_u32(&sh->drain), 0, p.status, p.timeout_cycles))
-                    ozg_drain_wait(smem_u32(&sh->drain), 0, p.status, p.timeout_cycles);
-            }
+            // all MMAs issued must complete before TMEM is freed: each issuer arrives on the
+            // drain barrier once its MMAs are done (at once if it issued none); if the first
+            // budget expires (FCI_ERR_TIMEOUT recorded) a second one follows before the
+            // deallocation goes ahead
+            if (issued) mma_commit(smem_u32(&sh->drain));
+            else mbar_arrive(smem_u32(&sh->drain));
+            if (!ozg_drain_wait(smem_u32(&sh->drain), 0, p.status, p.timeout_cycles))
+                ozg_drain_wait(smem_u32(&sh->drain), 0, p.status, p.timeout_cycles);
+        };
+        if (lane == 0) {
+            if (warp == 1) issuer(std::integral_constant<int, 0>{});
+            else issuer(std::integral_constant<int, 1>{});
         }
     } else {
         // ---------------------------------------------------------------- epilogue
@@ -285,7 +300,7 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
         // released at the end.
         constexpr int CH = OZG_N / (4 * ozg_epi_warps(S));  // 16-column chunks per warp: 2 or 1
         const int qd = warp & 3;
-        const int cw = 16 * CH * ((warp - 2) >> 2);
+        const int cw = 16 * CH * ((warp - 1 - OZG_ISSUERS) >> 2);
         const int row = 32 * qd + lane;
         constexpr int lowshift = W * (L0 - (S - 1));
         uint32_t tau = 0;

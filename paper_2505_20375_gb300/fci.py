@@ -113,6 +113,8 @@ _dav_request = _sig("davidson_request", [_vp, ctypes.POINTER(_vp), ctypes.POINTE
                                          ctypes.POINTER(_i32), ctypes.POINTER(_vp), ctypes.POINTER(_sz)])
 _dav_advance = _sig("davidson_advance", [_vp, ctypes.POINTER(_i32)])
 _dav_finish = _sig("davidson_finish", [_vp, _vp, ctypes.POINTER(_dbl), ctypes.POINTER(fci_davidson_log)])
+_cs_ws = _sig("fci_sigma_compressed_workspace_bytes", [_vp, _i64, ctypes.POINTER(_sz)])
+_cs_sigma = _sig("fci_sigma_compressed", [_vp, _vp, _vp, _i64, _vp, _vp, _i64, ctypes.POINTER(_i64), _vp, _sz, _vp])
 PHASES = ("gather", "contract", "scatter", "other")
 
 
@@ -281,6 +283,12 @@ class FCI:
                                  _stream(stream)))
         return out
 
+    def sigma_graph_into(self, x: int, y: int, precision, n_slices: int, ws: int, ws_bytes: int, stream=None):
+        """fci_sigma_graph on caller pointers: y = H x (DEVICE addresses) with the caller's
+        workspace, e.g. the sigma request of a step-wise Davidson solve."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        self._check(_sigma_graph(self._h, _vp(x), _vp(y), prec, n_slices, _vp(ws), ws_bytes, _stream(stream)))
+
     def clear_graphs(self):
         self._check(_clear_graphs(self._h))
 
@@ -349,6 +357,26 @@ class FCI:
             self._check(rc)
         its = [{k: getattr(iters[i], k) for k, _ in fci_davidson_iter._fields_} for i in range(log.n_iter)]
         return DavidsonResult(E.value, C, bool(log.converged), log.n_sigma, its, _gap_of(log))
+
+    def sigma_compressed(self, addr: torch.Tensor, val: torch.Tensor, capacity: int = None, stream=None):
+        """sigma = H C for a categorically compressed C on the DAS layout
+        (fci_sigma_compressed): addr (int64, ascending DAS target addresses) and val
+        (float64) on the device; returns sigma's support (ascending addresses) and values."""
+        addr = addr.to(self.device, torch.int64).contiguous()
+        val = val.to(self.device, torch.float64).contiguous()
+        nnz = addr.numel()
+        b = _sz()
+        self._check(_cs_ws(self._h, nnz, ctypes.byref(b)))
+        p, nb = self._workspace(b.value)
+        if capacity is None:
+            nm = self.info["n_ent_alpha"] + self.info["n_ent_beta"]
+            capacity = max(1, nnz * nm * nm)
+        out_a = torch.empty(capacity, dtype=torch.int64, device=self.device)
+        out_v = torch.empty(capacity, dtype=torch.float64, device=self.device)
+        n = _i64()
+        self._check(_cs_sigma(self._h, addr.data_ptr(), val.data_ptr(), nnz, out_a.data_ptr(), out_v.data_ptr(),
+                              capacity, ctypes.byref(n), p, nb, _stream(stream)))
+        return out_a[:n.value], out_v[:n.value]
 
     def sync_status(self, stream=None):
         """Synchronise and raise FCIError(FCI_ERR_TIMEOUT) if a device wait expired."""

@@ -1,23 +1,31 @@
 """Continuous-batching service for many Davidson solves on one GPU.
 
-Requests (a problem: integrals seed, active space, precision) arrive over time.  A
-request is admitted as soon as a slot is free and its device memory fits the budget;
-its C, sigma and subspace vectors then stay resident until it converges.  Each step,
-the sigma products that all active solves need go to the library in one grouped call
-(split-precision products with the same slice count share one persistent tcgen05
-launch), and every solve then takes its Davidson update (davidson_advance).  Each solve
-stages its sigma requests through two fixed vectors (staged_sigma), so while the set of
-active solves and their precisions do not change the grouped call is the same list
-every step and is replayed from a captured CUDA graph (fci_sigma_grouped_graph).  Solves that finish leave the batch and free their memory; waiting
-requests join at the next step.  Reported: time from arrival to converged energy
-(p50/p99) and aggregate determinants * sigma / s.
+Requests (a problem: integrals seed, active space, precision) arrive over time.  A host
+thread builds each request's handle (integrals, strings, DAS layout) as soon as it
+arrives, off the step loop.  A built request is admitted as soon as a slot is free and
+its device memory fits the budget; its C, sigma and subspace vectors then stay resident
+until it converges.  Active solves run in two lanes:
+  * split-precision solves (the mixed requests) share one stream: each step their sigma
+    products go to the library in one grouped call (products with the same slice count
+    share one persistent tcgen05 launch), replayed from a captured CUDA graph while the set
+    of solves and their precisions do not change (each solve stages its sigma requests
+    through two fixed vectors, staged_sigma), and every solve then takes its Davidson
+    update;
+  * FP64 solves each have a stream of their own: a solve whose sigma has finished takes its
+    update and launches its next sigma at once, so a slow FP64 product (the FP64 DAS
+    contraction runs on the FP64 pipe) never holds up the other solves.
+Solves that finish leave and free their memory; waiting requests join at once.  Reported:
+time from arrival to converged energy (p50/p99) and aggregate determinants * sigma / s.
 
 This is scheduling around the library's C ABI; every sigma build and every Davidson
 update runs in libfci's kernels.
 """
 from __future__ import annotations
 
+import collections
 import math
+import queue
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -89,8 +97,43 @@ def make_requests(n_req: int, rate: float, seed: int = 5, kinds=None):
 
 
 class _Active:
-    def __init__(self, req: Request, f: fci.FCI, stepper: fci.DavidsonStepper, admitted: float, nbytes: int):
+    def __init__(self, req: Request, f: fci.FCI, stepper: fci.DavidsonStepper, admitted: float, nbytes: int,
+                 stream=None):
         self.req, self.f, self.stepper, self.admitted, self.nbytes = req, f, stepper, admitted, nbytes
+        self.stream = stream      # FP64 lane: the solve's own stream (None: the split lane)
+        self.launched = False     # FP64 lane: a sigma product is in flight
+
+
+class _Builder(threading.Thread):
+    """Builds arrived requests' handles (integrals, strings, DAS layout, Davidson options
+    and workspace size) on a stream of its own, in arrival order."""
+
+    def __init__(self, server: "Server"):
+        super().__init__(daemon=True)
+        self.server = server
+        self.todo = queue.Queue()
+        self.ready = collections.deque()
+        self.lock = threading.Lock()
+        self.error = None
+
+    def run(self):
+        torch.cuda.set_device(self.server.device)
+        st = torch.cuda.Stream(self.server.device)
+        with torch.cuda.stream(st):
+            while True:
+                req = self.todo.get()
+                if req is None:
+                    return
+                try:
+                    f = self.server._build(req)
+                    opts = self.server._opts(f, req)
+                    nbytes = f.davidson_workspace_bytes(opts) + (8 << 20)
+                    st.synchronize()
+                except Exception as e:  # reported by the step loop
+                    self.error = e
+                    return
+                with self.lock:
+                    self.ready.append((req, f, opts, nbytes))
 
 
 @dataclass
@@ -101,8 +144,8 @@ class Server:
     tol_residual: float = 1e-5
     tol_energy: float = 1e-9
     split_slices: int = 3             # first phase of mixed requests
-    final_slices: int = 6             # FP64-class correction phase of FCI requests (error < 1e-11
-                                      # of ||sigma||); DAS requests correct in FP64
+    final_slices: int = 6             # FP64-class correction phase of mixed requests (error < 1e-11 of
+                                      # ||sigma||; the two-pass split form on the DAS layout)
     max_iter: int = 300
     use_graphs: bool = True           # replay the grouped sigma from captured CUDA graphs
     log: list = field(default_factory=list)
@@ -110,13 +153,9 @@ class Server:
     def _opts(self, f: fci.FCI, req: Request):
         kw = dict(max_iter=self.max_iter, tol_residual=self.tol_residual, tol_energy=self.tol_energy,
                   staged_sigma=self.use_graphs)
-        if req.mixed and req.kind == "fci" and req.n <= 15:
+        if req.mixed and ((req.kind == "fci" and req.n <= 15) or (req.kind == "das" and req.n <= 17)):
             return f.davidson_opts(**kw, precision="oz_bf16", n_slices=self.split_slices, switch_residual=1e-4,
                                    final_precision="oz_bf16", final_slices=self.final_slices)
-        if req.mixed and req.kind == "das" and req.n <= 17:
-            # the DAS split path takes at most 3 slices; the correction phase is FP64
-            return f.davidson_opts(**kw, precision="oz_bf16", n_slices=min(self.split_slices, 3),
-                                   switch_residual=1e-4, final_precision="fp64")
         return f.davidson_opts(**kw)
 
     def _build(self, req: Request):
@@ -145,53 +184,99 @@ class Server:
             free, _ = torch.cuda.mem_get_info(self.device)
             budget = int(0.6 * free)
         pending = sorted(requests, key=lambda r: r.arrival)
-        waiting, active, results = [], [], []
+        builder = _Builder(self)
+        builder.start()
+        lane_streams = []  # FP64 lanes' streams, reused
+        split, fp64, results = [], [], []
         used = 0
         t0 = clock()
         det_sigma = 0
         n_steps = 0
         signatures = set()
-        while pending or waiting or active:
-            now = clock() - t0
-            while pending and pending[0].arrival <= now:
-                waiting.append(pending.pop(0))
-            # admission: FIFO while a slot and the memory budget allow
-            while waiting and len(active) < self.max_active:
-                req = waiting[0]
-                f = self._build(req)
-                opts = self._opts(f, req)
-                nbytes = f.davidson_workspace_bytes(opts) + (8 << 20)
-                if active and used + nbytes > budget:
-                    f.close()
-                    break
-                waiting.pop(0)
-                st = fci.DavidsonStepper(f, opts, stream=stream)
-                active.append(_Active(req, f, st, clock() - t0, nbytes))
-                used += nbytes
-            if not active:
-                if pending:
-                    time.sleep(max(0.0, min(0.05, pending[0].arrival - (clock() - t0))))
-                continue
-            # one step: every active solve's sigma request in one grouped call
-            jobs = []
-            for a in active:
-                x, y, prec, sl, ws, wsb = a.stepper.request()
-                jobs.append((a.f, x, y, prec, sl, ws, wsb))
-                det_sigma += a.f.n_det
-            fci.sigma_grouped(jobs, stream=stream, graph=self.use_graphs)
-            signatures.add(tuple((id(j[0]), j[1], j[2], j[3], j[4], j[5]) for j in jobs))
-            n_steps += 1
-            still = []
-            for a in active:
-                if a.stepper.advance():
-                    r = a.stepper.finish()
-                    results.append(Result(a.req.rid, r.energy, r.converged, len(r.iterations), a.f.n_det, r.n_sigma,
-                                          a.req.arrival, a.admitted, clock() - t0, a.req.mixed, a.req.kind))
-                    used -= a.nbytes
-                    a.f.close()
-                else:
+
+        def finish(a):
+            nonlocal used
+            r = a.stepper.finish()
+            results.append(Result(a.req.rid, r.energy, r.converged, len(r.iterations), a.f.n_det, r.n_sigma,
+                                  a.req.arrival, a.admitted, clock() - t0, a.req.mixed, a.req.kind))
+            used -= a.nbytes
+            a.f.close()
+            if a.stream is not None:
+                lane_streams.append(a.stream)
+
+        try:
+            while pending or builder.todo.qsize() or builder.ready or split or fp64 or \
+                    len(results) < len(requests):
+                if builder.error is not None:
+                    raise builder.error
+                now = clock() - t0
+                while pending and pending[0].arrival <= now:
+                    builder.todo.put(pending.pop(0))
+                # admission: in arrival order while a slot and the memory budget allow
+                while len(split) + len(fp64) < self.max_active:
+                    with builder.lock:
+                        if not builder.ready:
+                            break
+                        req, f, opts, nbytes = builder.ready[0]
+                        if (split or fp64) and used + nbytes > budget:
+                            break
+                        builder.ready.popleft()
+                    lane = None
+                    if opts.precision == fci.FCI_PREC_FP64:
+                        lane = lane_streams.pop() if lane_streams else torch.cuda.Stream(self.device)
+                    st = fci.DavidsonStepper(f, opts, stream=lane if lane is not None else stream)
+                    a = _Active(req, f, st, clock() - t0, nbytes, lane)
+                    (fp64 if lane is not None else split).append(a)
+                    used += nbytes
+                if not split and not fp64:
+                    time.sleep(0.0005 if (builder.todo.qsize() or builder.ready) else
+                               max(0.0, min(0.02, pending[0].arrival - (clock() - t0))) if pending else 0.0005)
+                    continue
+                # split lane: one grouped sigma call for every split solve
+                if split:
+                    jobs = []
+                    for a in split:
+                        x, y, prec, sl, ws, wsb = a.stepper.request()
+                        jobs.append((a.f, x, y, prec, sl, ws, wsb))
+                        det_sigma += a.f.n_det
+                    fci.sigma_grouped(jobs, stream=stream, graph=self.use_graphs)
+                    signatures.add(tuple((id(j[0]), j[1], j[2], j[3], j[4], j[5]) for j in jobs))
+                    n_steps += 1
+                # FP64 lane: launch the sigma of every solve without one in flight, advance
+                # the solves whose sigma has finished
+                still = []
+                for a in fp64:
+                    if a.launched and a.stream.query():
+                        a.launched = False
+                        if a.stepper.advance():
+                            finish(a)
+                            continue
+                    if not a.launched:
+                        x, y, prec, sl, ws, wsb = a.stepper.request()
+                        if self.use_graphs:  # the solve's own sigma graph (fci_sigma_graph)
+                            a.f.sigma_graph_into(x, y, prec, sl, ws, wsb, stream=a.stream)
+                        else:
+                            fci.sigma_grouped([(a.f, x, y, prec, sl, ws, wsb)], stream=a.stream)
+                        det_sigma += a.f.n_det
+                        a.launched = True
                     still.append(a)
-            active = still
+                fp64 = still
+                # split lane: every solve takes its update (waits for the grouped sigma)
+                still = []
+                for a in split:
+                    if a.stepper.advance():
+                        finish(a)
+                    else:
+                        still.append(a)
+                split = still
+                if not split and fp64 and all(a.launched for a in fp64):
+                    time.sleep(0.0002)  # only FP64 products in flight: poll gently
+        finally:
+            builder.todo.put(None)
+            builder.join()
+            with builder.lock:
+                for _, f, _, _ in builder.ready:
+                    f.close()
         torch.cuda.synchronize()
         wall = clock() - t0
         lat = np.array([r.latency for r in results])
@@ -203,7 +288,7 @@ class Server:
             "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
             "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
             "converged": int(sum(r.converged for r in results)),
-            "distinct_job_lists": len(signatures),  # graph captures; the other steps replay
+            "distinct_job_lists": len(signatures),  # graph captures of the split lane; the other steps replay
         }
         if self.use_graphs:
             fci.clear_grouped_graphs()
@@ -217,3 +302,19 @@ def solve_alone(req: Request, server: Server):
                     split_slices=server.split_slices, final_slices=server.final_slices,
                     max_iter=server.max_iter, use_graphs=server.use_graphs).run([Request(**{**req.__dict__, "arrival": 0.0})])
     return res[0]
+
+
+def measure_capacity(server: Server, seed: int = 2000):
+    """Single-stream capacity of the request mix: one request of every shape in MIX, in
+    each precision, solved alone one after another; the mean time to energy of the mix
+    (uniform over shapes, half mixed precision) is the mean service time, and its inverse
+    the capacity in requests per second.  Returns (mean service seconds, per-request times)."""
+    times = {}
+    for i, m in enumerate(MIX):
+        for mixed in (False, True):
+            req = Request(rid=i, mixed=mixed, seed=seed + 2 * i + int(mixed), **{k: v for k, v in m.items()})
+            t0 = time.perf_counter()
+            solve_alone(req, server)
+            times[f"{m['kind']}{m['n']}_{'mixed' if mixed else 'fp64'}"] = time.perf_counter() - t0
+    return float(np.mean(list(times.values()))), times
+

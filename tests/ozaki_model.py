@@ -115,10 +115,11 @@ def sigma_model(h, g, n, na, nb, C, s, e_core=0.0, e_fp32=False):
 
 
 def das_sigma_model(h, g, spaces, ref, nel, max_transfer, C, s, e_core=0.0):
-    """Split sigma on the DAS layout (s <= 3, E stored in FP32).  The DAS sigma is the
-    FCI sigma of the zero-padded vector restricted to the DAS determinants (every
-    determinant one replacement away from a target one lies in the intermediate space),
-    so the model embeds C, applies sigma_model and restricts."""
+    """Split sigma on the DAS layout: the fused form (s <= 3) stores E rounded to FP32,
+    the two-pass form (s >= 4) keeps E_int exact in int64.  The DAS sigma is the FCI sigma
+    of the zero-padded vector restricted to the DAS determinants (every determinant one
+    replacement away from a target one lies in the intermediate space), so the model
+    embeds C, applies sigma_model and restricts."""
     from oracle import das as odas
 
     n = sum(spaces)
@@ -129,7 +130,7 @@ def das_sigma_model(h, g, spaces, ref, nel, max_transfer, C, s, e_core=0.0):
     addr = np.array([pos[int(d) & mask] * len(sa) + pos[int(d) >> n] for d in dets], dtype=np.int64)
     Cf = np.zeros(len(sa) ** 2)
     Cf[addr] = C
-    return sigma_model(h, g, n, nel, nel, Cf, s, e_core=0.0, e_fp32=True)[addr] + e_core * C
+    return sigma_model(h, g, n, nel, nel, Cf, s, e_core=0.0, e_fp32=s <= 3)[addr] + e_core * C
 
 
 def complex_contraction_matrix(h, g, n_el):

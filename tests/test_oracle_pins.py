@@ -431,3 +431,14 @@ def test_oracle_sigma_with_a_prebuilt_table_is_the_same_sigma():
     rows = np.array([len(dets) - 1, 0, 17, 17, 400])
     assert np.array_equal(t.sigma(hso, gso, c, e_core=0.7, rows=rows), full[rows])
     t.close()
+
+
+@pytest.mark.parametrize("spaces,ref,nel,T", [([2, 2, 2], [1, 1, 1], 3, 1), ([3, 3, 2], [1, 2, 1], 4, 1),
+                                              ([2, 3, 3], [1, 1, 2], 4, 2), ([4, 4, 4, 4], [1, 1, 1, 1], 4, 1)])
+def test_das_address_decoding_matches_the_enumeration(spaces, ref, nel, T):
+    """Decoding an address from the order's definition gives the determinant that the
+    enumeration of the whole space puts there (so it can stand in for the enumeration of
+    spaces too large to list, such as 24 orbitals in 4 x 6)."""
+    dets, _ = odas.das_dets(spaces, ref, ref, nel, nel, T)
+    idx = np.arange(len(dets)) if len(dets) < 20000 else np.unique(synth.Stream(3).bits(4000) % len(dets))
+    assert np.array_equal(odas.dets_of_addresses(spaces, ref, ref, nel, nel, T, idx), dets[idx])
