@@ -1,13 +1,13 @@
-// Kernel layout (one persistent CTA per SM, 352 or 608 threads):
+// Kernel layout (one persistent CTA per SM, 32 (1 + OZG_ISSUERS + 8 or 16) threads):
 //   warp 0     lane 0 issues the two bulk copies of each pipeline stage (A tile: s planes
 //              of 128 x 32, B tile: s planes of 64 x 32), completing on the stage's mbarrier;
-//   warps 1, 2 lane 0 of each issues the MMAs (M = 128, N = 64, K = 16) of half of the s
-//              level accumulators and commits (warp 1 also allocates TMEM): two issuing
-//              threads on two SM sub-partitions, because one thread issuing every MMA was
-//              measured at about 77 cycles per MMA against 48 for the bare instruction
-//              stream; the levels are dealt so that both issue about as many MMAs
-//              (level l, which takes s - l products, to issuer ((l + 1) / 2) mod 2);
-//   warps 3..  epilogue: 8 warps (two per TMEM lane quadrant, 32 columns each) when the
+//   warps 1 .. OZG_ISSUERS   lane 0 of each issues the MMAs (M = 128, N = 64, K = 16) of
+//              its share of the s level accumulators and commits (warp 1 also allocates
+//              TMEM): issuing threads on different SM sub-partitions, because one thread
+//              issuing every MMA was measured at about 77 cycles per MMA against 48 for the
+//              bare instruction stream; the levels are dealt so that every issuer issues
+//              about as many MMAs (level l takes s - l products; ozg_issuer);
+//   the rest   epilogue: 8 warps (two per TMEM lane quadrant, 32 columns each) when the
 //              accumulators are double-buffered (s <= 4), else 16 (four per quadrant,
 //              16 columns each), which read the levels three at a time and release each
 //              group as soon as it is in registers.
@@ -34,10 +34,22 @@ using namespace tc;
 // Epilogue warps: 8 (two per TMEM lane quadrant, 32 columns each) when the level
 // accumulators are double-buffered, 16 (four per quadrant, 16 columns each) otherwise.
 __host__ __device__ constexpr int ozg_epi_warps(int s) { return 2 * s * OZG_N <= 512 ? 8 : 16; }
-__host__ __device__ constexpr int ozg_threads(int s) { return 32 * (3 + ozg_epi_warps(s)); }
 constexpr int OZG_ISSUERS = 2;
-// The MMA issuer of level l (0 = the lowest kept level, which takes the most products).
-__host__ __device__ constexpr int ozg_issuer(int l) { return ((l + 1) >> 1) & 1; }
+__host__ __device__ constexpr int ozg_threads(int s) { return 32 * (1 + OZG_ISSUERS + ozg_epi_warps(s)); }
+// The MMA issuer of level l of s (level l takes s - l products): levels in order of their
+// product counts, each to the issuer with the fewest products so far.
+__host__ __device__ constexpr int ozg_issuer(int s, int l) {
+    int load[OZG_ISSUERS] = {};
+    int who = 0;
+    for (int k = 0; k <= l; ++k) {
+        int m = 0;
+        for (int e = 1; e < OZG_ISSUERS; ++e)
+            if (load[e] < load[m]) m = e;
+        load[m] += s - k;
+        who = m;
+    }
+    return who;
+}
 constexpr int OZG_MAX_STAGES = 6;
 constexpr size_t OZG_SMEM_MAX = 232448 - 1024;
 
@@ -64,7 +76,7 @@ struct OzgParams {
 
 struct OzgShared {
     uint64_t full[OZG_MAX_STAGES], empty[OZG_MAX_STAGES];
-    uint64_t acc_full[2], acc_empty[3];  // acc_empty: per buffer, or per level group (one buffer)
+    uint64_t acc_full[2], acc_empty[OZG_MAXS];  // acc_empty: per buffer, or per level group (one buffer)
     uint64_t drain, a_full;
     uint32_t tmem_base;
     int abort;
@@ -135,10 +147,10 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
     if (threadIdx.x == 0) {
         for (int r = 0; r < R; ++r) {
             mbar_init(smem_u32(&sh->full[r]), 1);
-            mbar_init(smem_u32(&sh->empty[r]), OZG_ISSUERS);  // both issuers' MMAs of the stage done
+            mbar_init(smem_u32(&sh->empty[r]), OZG_ISSUERS);  // every issuer's MMAs of the stage done
         }
         for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&sh->acc_full[b]), OZG_ISSUERS);
-        for (int b = 0; b < 3; ++b) mbar_init(smem_u32(&sh->acc_empty[b]), ozg_epi_warps(S));
+        for (int b = 0; b < OZG_MAXS; ++b) mbar_init(smem_u32(&sh->acc_empty[b]), ozg_epi_warps(S));
         mbar_init(smem_u32(&sh->drain), OZG_ISSUERS);
         mbar_init(smem_u32(&sh->a_full), 1);
         sh->abort = 0;
@@ -202,7 +214,7 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
     } else if (warp <= OZG_ISSUERS) {
         // ---------------------------------------------------------------- MMA issuers
         // ME (a compile-time copy of warp - 1): this thread issues the levels l with
-        // ozg_issuer(l) == ME, so each issuer's instruction stream holds its MMAs only.
+        // ozg_issuer(S, l) == ME, so each issuer's instruction stream holds its MMAs only.
         auto issuer = [&](auto me_c) {
             constexpr int ME = decltype(me_c)::value;
             // The ring slot and its parity advance with each stage (no division on the
@@ -242,7 +254,7 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
 #pragma unroll
                                 for (int i = S - 1 - j; i < S; ++i) {
                                     const int lv = i + j - (S - 1);
-                                    if (lv >= lo && lv < hi && ozg_issuer(lv) == ME)
+                                    if (lv >= lo && lv < hi && ozg_issuer(S, lv) == ME)
                                         mma_f16(dbase + (uint32_t)(lv * OZG_N),
                                                 as + (uint64_t)((i * A_PLANE + kk * 256) >> 4), b, idesc, acc_in);
                                 }
@@ -288,7 +300,8 @@ __global__ void __launch_bounds__(ozg_threads(S), 1) k_oz_gemm(const __grid_cons
         };
         if (lane == 0) {
             if (warp == 1) issuer(std::integral_constant<int, 0>{});
-            else issuer(std::integral_constant<int, 1>{});
+            else if (OZG_ISSUERS == 2 || warp == 2) issuer(std::integral_constant<int, 1>{});
+            else issuer(std::integral_constant<int, (OZG_ISSUERS > 2 ? 2 : 1)>{});
         }
     } else {
         // ---------------------------------------------------------------- epilogue
