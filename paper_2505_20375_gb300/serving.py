@@ -13,7 +13,9 @@ until it converges.  Active solves run in two lanes:
     update;
   * FP64 solves each have a stream of their own: a solve whose sigma has finished takes its
     update and launches its next sigma at once, so a slow FP64 product (the FP64 DAS
-    contraction runs on the FP64 pipe) never holds up the other solves.
+    contraction runs on the FP64 pipe) never holds up the other solves; the large FP64
+    products run on low-priority streams, the split lane and the small FP64 solves on high-
+    priority ones, so the block scheduler hands freed SMs to the short kernels first.
 Solves that finish leave and free their memory; waiting requests join at once.  Reported:
 time from arrival to converged energy (p50/p99) and aggregate determinants * sigma / s.
 
@@ -24,6 +26,7 @@ from __future__ import annotations
 
 import collections
 import math
+import os
 import queue
 import threading
 import time
@@ -118,7 +121,7 @@ class _Builder(threading.Thread):
 
     def run(self):
         torch.cuda.set_device(self.server.device)
-        st = torch.cuda.Stream(self.server.device)
+        st = torch.cuda.Stream(self.server.device, priority=0)  # set-up yields to the solves
         with torch.cuda.stream(st):
             while True:
                 req = self.todo.get()
@@ -148,6 +151,8 @@ class Server:
                                       # ||sigma||; the two-pass split form on the DAS layout)
     max_iter: int = 300
     use_graphs: bool = True           # replay the grouped sigma from captured CUDA graphs
+    fp64_low_priority: int = 20_000_000  # FP64 solves with n_det_intermediate x n_pair above run at low priority
+    fp64_das_chunk: int = 262_144     # FP64 DAS sigma in passes of at most this many intermediate determinants
     log: list = field(default_factory=list)
 
     def _opts(self, f: fci.FCI, req: Request):
@@ -173,8 +178,26 @@ class Server:
         return nb + (8 << 20)
 
     def run(self, requests, clock=time.perf_counter):
+        # The persistent tensor-core kernels of the split lane need whole SMs; a long FP64
+        # contraction on another stream keeps SMs partly busy until it ends, so the FP64 DAS
+        # products run in passes of bounded size (FCI_DAS_FP64_CHUNK_DETS, read by the
+        # library at each call) and no FP64 kernel holds the SMs for long.
+        old = os.environ.get("FCI_DAS_FP64_CHUNK_DETS")
+        if self.fp64_das_chunk > 0:
+            os.environ["FCI_DAS_FP64_CHUNK_DETS"] = str(self.fp64_das_chunk)
+        try:
+            return self._run_on_stream(requests, clock)
+        finally:
+            if self.fp64_das_chunk > 0:
+                if old is None:
+                    os.environ.pop("FCI_DAS_FP64_CHUNK_DETS", None)
+                else:
+                    os.environ["FCI_DAS_FP64_CHUNK_DETS"] = old
+
+    def _run_on_stream(self, requests, clock):
         torch.cuda.set_device(self.device)
-        stream = torch.cuda.Stream(self.device)  # graphs cannot be captured on the legacy stream
+        # graphs cannot be captured on the legacy stream; the split lane runs at high priority
+        stream = torch.cuda.Stream(self.device, priority=-1)
         with torch.cuda.stream(stream):
             return self._run(requests, clock, stream)
 
@@ -186,7 +209,7 @@ class Server:
         pending = sorted(requests, key=lambda r: r.arrival)
         builder = _Builder(self)
         builder.start()
-        lane_streams = []  # FP64 lanes' streams, reused
+        lane_streams = {-1: [], 0: []}  # FP64 lanes' streams by priority, reused
         split, fp64, results = [], [], []
         used = 0
         t0 = clock()
@@ -202,7 +225,7 @@ class Server:
             used -= a.nbytes
             a.f.close()
             if a.stream is not None:
-                lane_streams.append(a.stream)
+                lane_streams[a.prio].append(a.stream)
 
         try:
             while pending or builder.todo.qsize() or builder.ready or split or fp64 or \
@@ -221,11 +244,17 @@ class Server:
                         if (split or fp64) and used + nbytes > budget:
                             break
                         builder.ready.popleft()
-                    lane = None
+                    lane, prio = None, 0
                     if opts.precision == fci.FCI_PREC_FP64:
-                        lane = lane_streams.pop() if lane_streams else torch.cuda.Stream(self.device)
+                        # a large FP64 product (long FP64-pipe kernels) runs at low priority, so
+                        # that the kernels of the small solves take SMs as soon as blocks retire
+                        info = f.info
+                        prio = 0 if info["n_det_intermediate"] * info["n_pair"] > self.fp64_low_priority else -1
+                        pool = lane_streams[prio]
+                        lane = pool.pop() if pool else torch.cuda.Stream(self.device, priority=prio)
                     st = fci.DavidsonStepper(f, opts, stream=lane if lane is not None else stream)
                     a = _Active(req, f, st, clock() - t0, nbytes, lane)
+                    a.prio = prio
                     (fp64 if lane is not None else split).append(a)
                     used += nbytes
                 if not split and not fp64:
@@ -299,6 +328,7 @@ def solve_alone(req: Request, server: Server):
     """The same request through the same stepper path, on its own."""
     res, _ = Server(device=server.device, max_active=1, memory_budget=server.memory_budget,
                     tol_residual=server.tol_residual, tol_energy=server.tol_energy,
+                    fp64_das_chunk=server.fp64_das_chunk,
                     split_slices=server.split_slices, final_slices=server.final_slices,
                     max_iter=server.max_iter, use_graphs=server.use_graphs).run([Request(**{**req.__dict__, "arrival": 0.0})])
     return res[0]
