@@ -59,6 +59,9 @@ def _args():
     ap.add_argument("--path", default=None, choices=["fused", "gemm"],
                     help="alpha/beta split path for --profile-case (default: the library's choice)")
     ap.add_argument("--das-electrons", type=int, default=0, help="electrons per spin of a DAS --profile-case")
+    ap.add_argument("--profile-davidson", type=int, default=0,
+                    help="with --profile-case: run one Davidson solve of this many iterations (tolerances out of "
+                         "reach) at the given precision instead of sigma builds")
     ap.add_argument("--config-davidson", action="store_true",
                     help="also time Davidson to energy (FP64 vs split forms) on the DAS 16e and 24-spinor configs "
                          "(minutes: their FP64 sigma takes seconds)")
@@ -515,7 +518,7 @@ def run_ours(a, rank, world, local_rank):
     f.set_phase_timing(False)
     T = sum(step_ms) / 1e3
 
-    # end to end through the public call with HOST buffers (copies inside the timed region)
+    # end to end through the C ABI with HOST buffers (fci_sigma_host: copies inside the timed region)
     C_host = torch.from_numpy(c_np).pin_memory()
     S_host = torch.empty_like(C_host).pin_memory()
     f.sigma(C_host, precision=prec, n_slices=n_sl, out=S_host)
@@ -722,7 +725,8 @@ def run_ours(a, rank, world, local_rank):
                    "autotune": tuned,
                    "l2": "256 MB buffer written between timed steps (untimed)",
                    "setup_s": setup_s},
-        "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+        "e2e": {"value": e2e, "unit": METRIC, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
+                "call": "fci_sigma_host (C ABI: pinned host C and sigma, copies inside the call)"},
         "gpu_launches": int(launches),
         "roofline": roof,
         "phases_ms_per_step": {k: v["ms"] / a.steps for k, v in phases.items()},
@@ -758,6 +762,13 @@ def run_profile_case(a):
     c = torch.from_numpy(synth.random_vector(f.n_det, seed=7, complex_=f.is_complex)).cuda()
     prec = "fp64" if a.precision in ("fp64", "best") else a.precision
     sl = a.slices if prec != "fp64" else 0
+    if a.profile_davidson > 0:
+        r = f.davidson(precision=prec, n_slices=sl, final_precision=prec, final_slices=sl,
+                       max_iter=a.profile_davidson, tol_residual=1e-12, tol_energy=1e-14)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "davidson_iterations": len(r.iterations), "precision": prec,
+                          "n_slices": sl, "seconds_per_iteration": [i["seconds"] for i in r.iterations]}))
+        return
     o = f.sigma(c, precision=prec, n_slices=sl)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -163,6 +163,23 @@ int fci_sigma_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slic
 int fci_sigma(fci_handle h, const void *C, void *sigma, int n_vec, int precision,
               int n_slices, void *workspace, size_t workspace_bytes, fci_stream stream);
 
+/* Bytes of device workspace fci_sigma_host needs: room for n_vec vectors of C and of
+ * sigma on the device, then fci_sigma's own workspace. */
+int fci_sigma_host_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slices,
+                                   size_t *bytes);
+
+/* sigma = H C as fci_sigma, with C and sigma in HOST memory (n_vec x info.n_det,
+ * vector-major, same element types; must not overlap).  The call copies C into the
+ * front of the DEVICE workspace on `stream`, builds sigma there as fci_sigma does, copies
+ * it back into sigma_host and waits for the copy: pinned (page-locked) host buffers let
+ * the copies run asynchronously at the link rate, pageable ones work through the driver's
+ * staging.  Synchronous; it reports a device-side failure of this build as
+ * fci_sync_status does (FCI_ERR_TIMEOUT, sigma_host then holds NaN) and clears it.
+ *   workspace: DEVICE pointer, >= fci_sigma_host_workspace_bytes, 256-byte aligned. */
+int fci_sigma_host(fci_handle h, const void *C_host, void *sigma_host, int n_vec,
+                   int precision, int n_slices, void *workspace, size_t workspace_bytes,
+                   fci_stream stream);
+
 /* ---------------------------------------------------------------- Davidson */
 
 typedef struct {

@@ -103,26 +103,14 @@ __global__ void __launch_bounds__(256) k_das_scatter(DasDev d, int64_t a0, int64
     }
 }
 
-__global__ void k_das_diag(DasDev d, int n, const uint64_t *__restrict__ sa, const uint64_t *__restrict__ sb,
-                           const double *__restrict__ hd, const double *__restrict__ J,
-                           const double *__restrict__ K, double e_core, double *__restrict__ diag) {
+__global__ void k_das_diag(DasDev d, int n, int64_t nsa, const uint64_t *__restrict__ sa,
+                           const uint64_t *__restrict__ sb, const double *__restrict__ tab, double e_core,
+                           double *__restrict__ diag) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < d.n_det; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t Ai, Bi;
         int pb;
         das_strings(d, d.n_cat, i, Ai, Bi, pb);
-        const uint64_t A = sa[Ai], B = sb[Bi];
-        double e = e_core;
-        for (int p = 0; p < n; ++p) {
-            const int pa_ = (A >> p) & 1, pb_ = (B >> p) & 1;
-            if (!(pa_ | pb_)) continue;
-            e += (pa_ + pb_) * hd[p];
-            for (int q = 0; q < n; ++q) {
-                const int qa = (A >> q) & 1, qb = (B >> q) & 1;
-                const double j = J[p * n + q], k = K[p * n + q];
-                e += 0.5 * (pa_ * qa + pb_ * qb) * (j - k) + pa_ * qb * j;
-            }
-        }
-        diag[i] = e;
+        diag[i] = diag_from_strings(sa[Ai], sb[Bi], tab + (int64_t)Ai * (n + 1), tab + (nsa + Bi) * (n + 1), e_core);
     }
 }
 
@@ -390,8 +378,10 @@ int das_sigma_oz(fci_context *h, const double *C, double *sigma, int n_slices, v
 }
 
 cudaError_t launch_diag_das(const fci_context *h, double *diag, cudaStream_t s) {
-    k_das_diag<<<grid_for(h->das.n_det), 256, 0, s>>>(make_dev(h), h->n_orb, h->d_str_a, h->d_str_b, h->d_hd,
-                                                      h->d_J, h->d_K, h->e_core, diag);
+    cudaError_t e = launch_diag_strings(h, s);
+    if (e != cudaSuccess) return e;
+    k_das_diag<<<grid_for(h->das.n_det), 256, 0, s>>>(make_dev(h), h->n_orb, h->nsa, h->d_str_a, h->d_str_b,
+                                                      h->d_dstr, h->e_core, diag);
     return cudaGetLastError();
 }
 

@@ -32,41 +32,45 @@ struct dav_scalars {      // device-resident scalars, read back each iteration
     double pad;
 };
 
-// partial[b][i] (complex: 2 doubles) = sum over this block's slice of conj(V_i) x
-template <bool CPLX>
+// partial[b][i] (complex: 2 doubles) = sum over this block's slice of conj(V_i) x, for
+// i < k <= KB: KB (a power of two, at least k) sizes the accumulator arrays, so a call
+// with few vectors keeps few registers and many warps resident.
+template <bool CPLX, int KB>
 __global__ void __launch_bounds__(RED_THREADS) k_multidot(const double *__restrict__ V, int64_t ldv, int k,
                                                           const double *__restrict__ x, int64_t n,
                                                           double *__restrict__ partial) {
-    __shared__ double red[RED_THREADS / 32][2 * KMAX];
-    double acc_re[KMAX], acc_im[KMAX];
+    __shared__ double red[RED_THREADS / 32][2 * KB];
+    double acc_re[KB], acc_im[CPLX ? KB : 1];
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i) { acc_re[i] = 0.0; acc_im[i] = 0.0; }
+    for (int i = 0; i < KB; ++i) acc_re[i] = 0.0;
+#pragma unroll
+    for (int i = 0; i < (CPLX ? KB : 1); ++i) acc_im[i] = 0.0;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         if (CPLX) {
             const double xr = x[2 * j], xi = x[2 * j + 1];
 #pragma unroll
-            for (int i = 0; i < KMAX; ++i) {
+            for (int i = 0; i < KB; ++i) {
                 if (i < k) {
                     const double vr = V[i * 2 * ldv + 2 * j], vi = V[i * 2 * ldv + 2 * j + 1];
                     acc_re[i] = fma(vr, xr, fma(vi, xi, acc_re[i]));
-                    acc_im[i] = fma(vr, xi, fma(-vi, xr, acc_im[i]));
+                    acc_im[CPLX ? i : 0] = fma(vr, xi, fma(-vi, xr, acc_im[CPLX ? i : 0]));
                 }
             }
         } else {
             const double xr = x[j];
 #pragma unroll
-            for (int i = 0; i < KMAX; ++i)
+            for (int i = 0; i < KB; ++i)
                 if (i < k) acc_re[i] = fma(V[i * ldv + j], xr, acc_re[i]);
         }
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < KMAX; ++i) {
+    for (int i = 0; i < KB; ++i) {
         if (i >= k) break;
-        double a = acc_re[i], b = acc_im[i];
+        double a = acc_re[i], b = CPLX ? acc_im[CPLX ? i : 0] : 0.0;
         for (int o = 16; o; o >>= 1) {
             a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-            b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+            if (CPLX) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
         }
         if (lane == 0) { red[wid][2 * i] = a; red[wid][2 * i + 1] = b; }
     }
@@ -78,13 +82,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_multidot(const double *__restri
     }
 }
 
-// out[i] (complex) = sum_b partial[b][i]; fixed order, so the result is reproducible.
+// Sum over the nb block partials of a reduction in a fixed order (lane l adds blocks l,
+// l + 32, ..., then a butterfly over the lanes), so every result is reproducible.
+__device__ __forceinline__ double warp_sum_blocks(const double *__restrict__ p, int64_t stride, int nb) {
+    const int lane = threadIdx.x & 31;
+    double a = 0.0;
+    for (int b = lane; b < nb; b += 32) a += p[(int64_t)b * stride];
+    for (int o = 16; o; o >>= 1) a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    return a;
+}
+
+// out[i] (complex) = sum_b partial[b][i], one warp per entry.
 __global__ void k_reduce_partial(const double *__restrict__ partial, int nb, int k, double *__restrict__ out) {
-    const int i = threadIdx.x;
-    if (i >= 2 * k) return;
-    double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += partial[(int64_t)b * 2 * KMAX + i];
-    out[i] = s;
+    for (int i = threadIdx.x >> 5; i < 2 * k; i += blockDim.x >> 5) {
+        const double a = warp_sum_blocks(partial + i, 2 * KMAX, nb);
+        if ((threadIdx.x & 31) == 0) out[i] = a;
+    }
 }
 
 // out = sum_i y_i V_i  (+ beta * out when accumulate), y complex as 2 doubles per entry.
@@ -177,12 +190,19 @@ __global__ void __launch_bounds__(RED_THREADS) k_residual(double *__restrict__ c
 }
 
 __global__ void k_reduce_residual(const double *__restrict__ partial, int nb, dav_scalars *__restrict__ out) {
-    if (threadIdx.x != 0) return;
+    const int lane = threadIdx.x & 31;
     double a = 0, b = 0, m = 0;
-    for (int i = 0; i < nb; ++i) { a += partial[i * 4]; b += partial[i * 4 + 1]; m = fmax(m, partial[i * 4 + 2]); }
-    out->rnorm2 = a;
-    out->snorm2 = b;
-    out->maxdc = m;
+    for (int i = lane; i < nb; i += 32) { a += partial[i * 4]; b += partial[i * 4 + 1]; m = fmax(m, partial[i * 4 + 2]); }
+    for (int o = 16; o; o >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        m = fmax(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    }
+    if (lane == 0) {
+        out->rnorm2 = a;
+        out->snorm2 = b;
+        out->maxdc = m;
+    }
 }
 
 // Compression-compatible threshold: t_i = 0 where |t_i| < eps ||s||.
@@ -217,10 +237,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_norm2(const double *__restrict_
 }
 
 __global__ void k_reduce_norm(const double *__restrict__ partial, int nb, double *__restrict__ out) {
-    if (threadIdx.x != 0) return;
-    double s = 0;
-    for (int i = 0; i < nb; ++i) s += partial[i];
-    *out = s;
+    const double a = warp_sum_blocks(partial, 1, nb);
+    if (threadIdx.x == 0) *out = a;
 }
 
 // x *= 1/sqrt(*n2) (or *scale directly when n2 == nullptr)
@@ -394,23 +412,45 @@ __global__ void __launch_bounds__(JAC_THREADS) k_jacobi(const double *__restrict
 #undef Q
 
 // argmin of diag (lowest index on ties) -> unit vector
-__global__ void k_argmin(const double *__restrict__ d, int64_t n, int64_t *__restrict__ out) {
-    __shared__ double bv[256];
-    __shared__ int64_t bi[256];
-    double v = INFINITY;
-    int64_t idx = 0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
-        if (d[j] < v) { v = d[j]; idx = j; }
-    bv[threadIdx.x] = v;
-    bi[threadIdx.x] = idx;
+// Index of the smallest diagonal element (the lowest index among equal ones), in two
+// passes: per block (value, index) into part, then one block over the nb block results.
+__device__ __forceinline__ void argmin_merge(double &v, int64_t &i, double v2, int64_t i2) {
+    if (v2 < v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+__device__ void argmin_block(double v, int64_t idx, double *bv, int64_t *bi) {
+    for (int o = 16; o; o >>= 1)
+        argmin_merge(v, idx, __shfl_xor_sync(0xFFFFFFFFu, v, o), __shfl_xor_sync(0xFFFFFFFFu, idx, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) { bv[wid] = v; bi[wid] = idx; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double best = INFINITY;
-        int64_t b = 0;
-        for (int i = 0; i < (int)blockDim.x; ++i)
-            if (bv[i] < best || (bv[i] == best && bi[i] < b)) { best = bv[i]; b = bi[i]; }
-        *out = b;
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) argmin_merge(v, idx, bv[w], bi[w]);
+        bv[0] = v;
+        bi[0] = idx;
     }
+}
+__global__ void __launch_bounds__(256) k_argmin_part(const double *__restrict__ d, int64_t n, double *__restrict__ part) {
+    __shared__ double bv[8];
+    __shared__ int64_t bi[8];
+    double v = INFINITY;
+    int64_t idx = INT64_MAX;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        if (d[j] < v) { v = d[j]; idx = j; }
+    argmin_block(v, idx, bv, bi);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = bv[0];
+        part[2 * blockIdx.x + 1] = __longlong_as_double((long long)bi[0]);
+    }
+}
+__global__ void __launch_bounds__(256) k_argmin_final(const double *__restrict__ part, int nb, int64_t *__restrict__ out) {
+    __shared__ double bv[8];
+    __shared__ int64_t bi[8];
+    double v = INFINITY;
+    int64_t idx = INT64_MAX;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        argmin_merge(v, idx, part[2 * b], (int64_t)__double_as_longlong(part[2 * b + 1]));
+    argmin_block(v, idx, bv, bi);
+    if (threadIdx.x == 0) *out = bi[0] == INT64_MAX ? 0 : bi[0];
 }
 
 // splitmix64 (Steele, Lea and Flood 2014, "Fast splittable pseudorandom number
@@ -483,10 +523,24 @@ struct fci_davidson_state {
     double *Vk(int i) { return (double *)((char *)V + (size_t)i * vec); }
     double *Sk(int i) { return (double *)((char *)S + (size_t)i * vec); }
 
+    // vectors i0 .. i0 + kk - 1 of Vb into entries i0 .. of each block's partial row
+    template <int KB>
+    void multidot_kb(const double *Vb, int i0, int kk, const double *x) {
+        const double *v0 = Vb + (size_t)i0 * (cplx ? 2 : 1) * ldv;
+        if (cplx) k_multidot<true, KB><<<vb, RED_THREADS, 0, s>>>(v0, ldv, kk, x, n, partial + 2 * i0);
+        else k_multidot<false, KB><<<vb, RED_THREADS, 0, s>>>(v0, ldv, kk, x, n, partial + 2 * i0);
+    }
+    // <V_i|x> for i < kk: up to 16 vectors per pass (more would cost occupancy)
     cudaError_t multidot(const double *Vb, int kk, const double *x, double *out) {
-        if (cplx) k_multidot<true><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, kk, x, n, partial);
-        else k_multidot<false><<<vb, RED_THREADS, 0, s>>>(Vb, ldv, kk, x, n, partial);
-        k_reduce_partial<<<1, 64, 0, s>>>(partial, vb, kk, out);
+        if (kk <= 1) multidot_kb<1>(Vb, 0, kk, x);
+        else if (kk <= 4) multidot_kb<4>(Vb, 0, kk, x);
+        else if (kk <= 8) multidot_kb<8>(Vb, 0, kk, x);
+        else if (kk <= 16) multidot_kb<16>(Vb, 0, kk, x);
+        else {
+            multidot_kb<16>(Vb, 0, 16, x);
+            multidot_kb<16>(Vb, 16, kk - 16, x);
+        }
+        k_reduce_partial<<<1, 256, 0, s>>>(partial, vb, kk, out);
         return cudaGetLastError();
     }
     cudaError_t lincomb(const double *Vb, int kk, const double *yy, double scale, double *out, int acc) {
@@ -570,7 +624,8 @@ struct fci_davidson_state {
         if (guess) {
             FCI_CUDA(h, cudaMemcpyAsync(Vk(0), guess, (size_t)n * esz, cudaMemcpyDeviceToDevice, s));
         } else {
-            k_argmin<<<1, 256, 0, s>>>(diag, n, argmin);
+            k_argmin_part<<<vb, 256, 0, s>>>(diag, n, partial);
+            k_argmin_final<<<1, 256, 0, s>>>(partial, (int)vb, argmin);
             k_set_start<<<vb, RED_THREADS, 0, s>>>(Vk(0), nreal, cplx, argmin, o.start_mix);
         }
         FCI_CUDA(h, normalize(Vk(0), nrm));

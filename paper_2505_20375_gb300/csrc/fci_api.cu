@@ -162,12 +162,14 @@ static void free_strings(fci_context *h) {
     fci_dev_free(h->d_str_a); fci_dev_free(h->d_str_b);
     fci_dev_free(h->d_rep_a); fci_dev_free(h->d_rep_b);
     fci_dev_free(h->d_pair_a); fci_dev_free(h->d_pair_b);
+    fci_dev_free(h->d_dstr);
     fci_dev_free(h->d_G); fci_dev_free(h->d_hd); fci_dev_free(h->d_J); fci_dev_free(h->d_K);
     fci_dev_free(h->d_Gs);
     fci_dev_free(h->d_Gt);
     h->d_str_a = h->d_str_b = nullptr;
     h->d_rep_a = h->d_rep_b = nullptr;
     h->d_pair_a = h->d_pair_b = nullptr;
+    h->d_dstr = nullptr;
     h->d_G = h->d_hd = h->d_J = h->d_K = nullptr;
     h->d_Gs = nullptr;
     h->Gs_slices = 0;
@@ -464,6 +466,7 @@ int fci_build_strings(fci_handle h, int n_alpha, int n_beta, fci_stream stream) 
         h->npair_pad = (h->npair + 15) / 16 * 16;
         if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_pair_a, (size_t)nsa * h->npair_pad * 4);
         if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_pair_b, (size_t)nsb * h->npair_pad * 4);
+        if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_dstr, (size_t)(nsa + nsb) * (n + 1) * 8);
         if (rc) { free_strings(h); return rc; }
         FCI_CUDA(h, launch_repl_table(n, n_alpha, nsa, h->d_str_a, h->d_binom, h->nent_a, 1, h->d_rep_a, h->d_pair_a, h->npair_pad, s));
         FCI_CUDA(h, launch_repl_table(n, n_beta, nsb, h->d_str_b, h->d_binom, h->nent_b, 1, h->d_rep_b, h->d_pair_b, h->npair_pad, s));
@@ -540,6 +543,47 @@ int fci_sigma(fci_handle h, const void *C, void *sigma, int n_vec, int precision
         if (rc) return rc;
     }
     return FCI_OK;
+}
+
+// Device bytes of n_vec vectors, rounded to the workspace alignment.
+static size_t host_vec_bytes(const fci_context *h, int n_vec) {
+    const int64_t nd = h->das_active ? h->das.n_det : h->ndet;
+    const size_t esz = h->dtype == FCI_C128 ? 16 : 8;
+    return ((size_t)nd * esz * (size_t)n_vec + 255) & ~(size_t)255;
+}
+
+int fci_sigma_host_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slices, size_t *bytes) {
+    if (!h || !bytes) return fci_fail(h, FCI_ERR_ARG, "NULL argument");
+    if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "no strings built");
+    if (n_vec < 0) return fci_fail(h, FCI_ERR_ARG, "bad n_vec");
+    *bytes = 2 * host_vec_bytes(h, n_vec) + sigma_ws_bytes(h, precision, n_slices);
+    return FCI_OK;
+}
+
+int fci_sigma_host(fci_handle h, const void *C_host, void *sigma_host, int n_vec, int precision, int n_slices,
+                   void *ws, size_t ws_bytes, fci_stream stream) {
+    if (!h) return fci_fail(nullptr, FCI_ERR_ARG, "NULL handle");
+    if (h->mode == FCI_MODE_NONE) return fci_fail(h, FCI_ERR_STATE, "no strings built");
+    if (!C_host || !sigma_host || n_vec < 0) return fci_fail(h, FCI_ERR_ARG, "bad C/sigma/n_vec");
+    const size_t vb = host_vec_bytes(h, n_vec);
+    const size_t need = 2 * vb + sigma_ws_bytes(h, precision, n_slices);
+    if (!ws || ws_bytes < need) return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes", ws_bytes, need);
+    if (((uintptr_t)ws & 255) != 0) return fci_fail(h, FCI_ERR_ARG, "workspace not 256-byte aligned");
+    const int64_t nd = h->das_active ? h->das.n_det : h->ndet;
+    const size_t bytes = (size_t)nd * (h->dtype == FCI_C128 ? 16 : 8) * (size_t)n_vec;
+    const char *c0 = (const char *)C_host, *s0 = (const char *)sigma_host;
+    if (bytes && c0 < s0 + bytes && s0 < c0 + bytes) return fci_fail(h, FCI_ERR_ARG, "C and sigma overlap");
+    int rc = set_dev(h);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *Cd = (char *)ws, *Sd = Cd + vb;
+    FCI_CUDA(h, cudaMemcpyAsync(Cd, C_host, bytes, cudaMemcpyHostToDevice, s));
+    if ((rc = fci_sigma(h, Cd, Sd, n_vec, precision, n_slices, Sd + vb, ws_bytes - 2 * vb, stream))) {
+        cudaStreamSynchronize(s);  // the copy in flight still reads C_host
+        return rc;
+    }
+    FCI_CUDA(h, cudaMemcpyAsync(sigma_host, Sd, bytes, cudaMemcpyDeviceToHost, s));
+    return fci_sync_status(h, stream);
 }
 
 void fci_davidson_default_opts(fci_davidson_opts *o) {

@@ -24,6 +24,20 @@ __host__ __device__ inline uint32_t rep_target(uint64_t e) { return (uint32_t)e;
 __host__ __device__ inline int rep_a(uint64_t e) { return (int)((e >> 32) & 0xFF); }
 __host__ __device__ inline int rep_b(uint64_t e) { return (int)((e >> 40) & 0xFF); }
 __host__ __device__ inline int rep_neg(uint64_t e) { return (int)((e >> 48) & 1); }
+
+#ifdef __CUDACC__
+// Diagonal element of the determinant of strings A (alpha) and B (beta) from their rows
+// ta, tb of the per-string table (d_dstr: row[0] the string's own energy, row[1 + p] =
+// sum_{q in string} J_pq): e_core + (e(A) + e(B)) + 1/2 (sum_{p in A} j_B(p) + sum_{p in B}
+// j_A(p)), symmetric under exchanging A and B bit for bit.
+__device__ __forceinline__ double diag_from_strings(uint64_t A, uint64_t B, const double *__restrict__ ta,
+                                                    const double *__restrict__ tb, double e_core) {
+    double x1 = 0.0, x2 = 0.0;
+    for (uint64_t m = A; m; m &= m - 1) x1 += tb[__ffsll((long long)m)];  // row[1 + p], p = ffs - 1
+    for (uint64_t m = B; m; m &= m - 1) x2 += ta[__ffsll((long long)m)];
+    return e_core + ((ta[0] + tb[0]) + 0.5 * (x1 + x2));
+}
+#endif
 __host__ __device__ inline int rep_pair(uint64_t e) { return (int)(e >> 49); }
 
 // Packed index of the unordered orbital pair {a, b}.
@@ -100,6 +114,10 @@ struct fci_context {
     double *d_G = nullptr;
     // diagonal helpers: h_pp, J_pq = (pp|qq), K_pq = (pq|qp) (real parts)
     double *d_hd = nullptr, *d_J = nullptr, *d_K = nullptr;
+    // per alpha and beta string (alpha strings first, n_orb + 1 doubles each): the string's
+    // own one- and two-electron diagonal energy, then sum_{q in string} J_pq for every p;
+    // filled by launch_diag_strings before each use of the diagonal (alpha/beta modes)
+    double *d_dstr = nullptr;
     // Ozaki split of G (bf16 digit slices, canonical UMMA layout) and its scale
     void *d_Gs = nullptr;
     int Gs_slices = 0;
@@ -182,6 +200,8 @@ cudaError_t launch_scatter_fci_r64(const fci_context *h, const double *E, const 
                                    double *sigma, cudaStream_t s);
 cudaError_t launch_dgemm(int M, int64_t N, int K, const double *A, const double *B, int64_t ldb,
                          double *C, int64_t ldc, cudaStream_t s);
+// Per-string diagonal tables (d_dstr) from the current integrals.
+cudaError_t launch_diag_strings(const fci_context *h, cudaStream_t s);
 cudaError_t launch_diag_fci(const fci_context *h, double *diag, cudaStream_t s);
 
 // spinor.cu

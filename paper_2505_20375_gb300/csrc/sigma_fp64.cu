@@ -127,26 +127,43 @@ __global__ void __launch_bounds__(256) k_dgemm(int M, int64_t N, int K, const do
 
 // H_II = sum_{p in a} h_pp + sum_{p in b} h_pp + 1/2 sum_{p,q in a} (J_pq - K_pq)
 //      + 1/2 sum_{p,q in b} (J_pq - K_pq) + sum_{p in a, q in b} J_pq
+// (Slater-Condon, the diagonal element).  The first four terms split into a per-string
+// energy e(S) = sum_{p in S} h_pp + 1/2 sum_{p,q in S} (J_pq - K_pq), the last is the
+// cross term X(a, b) = sum_{p in a} j_b(p) with j_S(p) = sum_{q in S} J_pq; both come from
+// a table with one row per string (k_diag_strings), so a determinant costs O(n_el) adds.
+// The cross term is taken as 1/2 (sum_{p in a} j_b(p) + sum_{p in b} j_a(p)) and the
+// string energies are added as (e(a) + e(b)): H_II is then exactly symmetric under
+// exchanging the alpha and beta strings, as the operator is.
+__global__ void k_diag_strings(int64_t nsa, int64_t nsb, int n, const uint64_t *__restrict__ sa,
+                               const uint64_t *__restrict__ sb, const double *__restrict__ hd,
+                               const double *__restrict__ J, const double *__restrict__ K,
+                               double *__restrict__ tab) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nsa + nsb; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t S = s < nsa ? sa[s] : sb[s - nsa];
+        double *row = tab + s * (n + 1);
+        double e = 0.0;
+        for (int p = 0; p < n; ++p) {
+            double jp = 0.0;
+            for (int q = 0; q < n; ++q)
+                if ((S >> q) & 1) jp += J[p * n + q];
+            row[1 + p] = jp;
+            if (!((S >> p) & 1)) continue;
+            e += hd[p];
+            for (int q = 0; q < n; ++q)
+                if ((S >> q) & 1) e += 0.5 * (J[p * n + q] - K[p * n + q]);
+        }
+        row[0] = e;
+    }
+}
+
 __global__ void k_diag_fci(int64_t nsa, int64_t nsb, int n, const uint64_t *__restrict__ sa,
-                           const uint64_t *__restrict__ sb, const double *__restrict__ hd,
-                           const double *__restrict__ J, const double *__restrict__ K,
-                           double e_core, double *__restrict__ diag) {
+                           const uint64_t *__restrict__ sb, const double *__restrict__ tab, double e_core,
+                           double *__restrict__ diag) {
     const int64_t ndet = nsa * nsb;
     for (int64_t det = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; det < ndet;
          det += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t A = sa[det / nsb], B = sb[det % nsb];
-        double e = e_core;
-        for (int p = 0; p < n; ++p) {
-            const int pa = (A >> p) & 1, pb = (B >> p) & 1;
-            if (!(pa | pb)) continue;
-            e += (pa + pb) * hd[p];
-            for (int q = 0; q < n; ++q) {
-                const int qa = (A >> q) & 1, qb = (B >> q) & 1;
-                const double j = J[p * n + q], k = K[p * n + q];
-                e += 0.5 * (pa * qa + pb * qb) * (j - k) + pa * qb * j;
-            }
-        }
-        diag[det] = e;
+        const int64_t ia = det / nsb, ib = det - ia * nsb;
+        diag[det] = diag_from_strings(sa[ia], sb[ib], tab + ia * (n + 1), tab + (nsa + ib) * (n + 1), e_core);
     }
 }
 
@@ -181,10 +198,18 @@ cudaError_t launch_dgemm(int M, int64_t N, int K, const double *A, const double 
     return cudaGetLastError();
 }
 
+cudaError_t launch_diag_strings(const fci_context *h, cudaStream_t s) {
+    const int64_t ns = h->nsa + h->nsb;
+    k_diag_strings<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ns, 128), 152 * 8)), 128, 0, s>>>(
+        h->nsa, h->nsb, h->n_orb, h->d_str_a, h->d_str_b, h->d_hd, h->d_J, h->d_K, h->d_dstr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_diag_fci(const fci_context *h, double *diag, cudaStream_t s) {
+    cudaError_t e = launch_diag_strings(h, s);
+    if (e != cudaSuccess) return e;
     const int64_t ndet = h->nsa * h->nsb;
     unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(ndet, 256), 152 * 32);
-    k_diag_fci<<<blocks, 256, 0, s>>>(h->nsa, h->nsb, h->n_orb, h->d_str_a, h->d_str_b, h->d_hd,
-                                      h->d_J, h->d_K, h->e_core, diag);
+    k_diag_fci<<<blocks, 256, 0, s>>>(h->nsa, h->nsb, h->n_orb, h->d_str_a, h->d_str_b, h->d_dstr, h->e_core, diag);
     return cudaGetLastError();
 }

@@ -79,6 +79,8 @@ _das = _sig("das_build_categories", [_vp, _i32, _vp, _vp, _vp, _i32, _vp])
 _diag = _sig("fci_diagonal", [_vp, _vp, _vp])
 _ws = _sig("fci_sigma_workspace_bytes", [_vp, _i32, _i32, _i32, ctypes.POINTER(_sz)])
 _sigma = _sig("fci_sigma", [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _sz, _vp])
+_host_ws = _sig("fci_sigma_host_workspace_bytes", [_vp, _i32, _i32, _i32, ctypes.POINTER(_sz)])
+_sigma_host = _sig("fci_sigma_host", [_vp, _vp, _vp, _i32, _i32, _i32, _vp, _sz, _vp])
 _dav_defaults = _sig("fci_davidson_default_opts", [ctypes.POINTER(fci_davidson_opts)], None)
 _dav_ws = _sig("fci_davidson_workspace_bytes", [_vp, ctypes.POINTER(fci_davidson_opts), ctypes.POINTER(_sz)])
 _davidson = _sig("davidson_solve", [_vp, ctypes.POINTER(fci_davidson_opts), _vp, ctypes.POINTER(_dbl),
@@ -255,24 +257,29 @@ class FCI:
 
     def sigma(self, C: torch.Tensor, precision: str = "fp64", n_slices: int = 0, out: torch.Tensor = None,
               stream=None) -> torch.Tensor:
-        """sigma = H C.  C: (n_det,) or (n_vec, n_det) on the device, or on the host
-        (then copied in and the result copied back, both inside this call)."""
-        host = C.device.type == "cpu"
-        Cd = C.to(self.device, non_blocking=True) if host else C
-        Cd = Cd.contiguous()
-        if Cd.dtype != self.vector_dtype():
+        """sigma = H C.  C: (n_det,) or (n_vec, n_det) on the device (fci_sigma), or on the
+        host (fci_sigma_host: the library copies C in and sigma back inside the call)."""
+        if C.dtype != self.vector_dtype():
             raise TypeError(f"C must be {self.vector_dtype()}")
-        n_vec = 1 if Cd.dim() == 1 else Cd.shape[0]
-        if Cd.shape[-1] != self.n_det:
+        n_vec = 1 if C.dim() == 1 else C.shape[0]
+        if C.shape[-1] != self.n_det:
             raise ValueError("C has the wrong length")
-        res = torch.empty_like(Cd) if (out is None or host) else out
+        if C.device.type == "cpu":
+            Ch = C.contiguous()
+            dst = out if out is not None else torch.empty_like(Ch, pin_memory=Ch.is_pinned())
+            if dst.device.type != "cpu" or not dst.is_contiguous() or dst.shape != Ch.shape:
+                raise ValueError("out must be a contiguous host tensor of C's shape")
+            b = _sz()
+            self._check(_host_ws(self._h, n_vec, PRECISIONS[precision], n_slices, ctypes.byref(b)))
+            p, nb = self._workspace(b.value)
+            self._check(_sigma_host(self._h, Ch.data_ptr(), dst.data_ptr(), n_vec, PRECISIONS[precision], n_slices,
+                                    p, nb, _stream(stream)))
+            return dst
+        Cd = C.contiguous()
+        res = torch.empty_like(Cd) if out is None else out
         p, nb = self._workspace(self.sigma_workspace_bytes(precision, n_slices, n_vec))
         self._check(_sigma(self._h, Cd.data_ptr(), res.data_ptr(), n_vec, PRECISIONS[precision], n_slices,
                            p, nb, _stream(stream)))
-        if host:
-            dst = out if out is not None else torch.empty_like(C, pin_memory=C.is_pinned())
-            dst.copy_(res, non_blocking=False)
-            return dst
         return res
 
     def sigma_graph(self, C: torch.Tensor, out: torch.Tensor, precision: str = "fp64", n_slices: int = 0,

@@ -53,6 +53,18 @@ def test_diagonal(fci_lib, n, na, nb):
     assert np.max(np.abs(d - ref)) < 1e-12
 
 
+def test_diagonal_alpha_beta_exchange_symmetric(fci_lib):
+    """The spin-free H is invariant under exchanging the alpha and beta strings, so with
+    n_alpha = n_beta H_(a,b),(a,b) = H_(b,a),(b,a); the diagonal kernel keeps this bit for
+    bit (the start vector's tie-break between the two determinants depends on it)."""
+    p = fci_problem(8, 4, 4, seed=17, e_core=0.3)
+    f = gpu_fci(p)
+    d = f.diagonal().cpu().numpy().reshape(70, 70)
+    assert np.array_equal(d, d.T)
+    ref = oracle.diag(p["hso"], p["gso"], p["dets"]) + p["e_core"]
+    assert np.max(np.abs(d.reshape(-1) - ref)) < 1e-12
+
+
 # ------------------------------------------------------------------- sigma
 
 @pytest.mark.parametrize("n,na,nb", [(1, 1, 1), (2, 1, 1), (3, 2, 1), (5, 0, 3), (6, 3, 3), (8, 4, 4),
@@ -88,6 +100,26 @@ def test_sigma_fp64_batched_and_host_buffers(fci_lib):
         ref = oracle.sigma(p["hso"], p["gso"], p["dets"], C[i])
         assert rel_inf(S[i], ref) <= SIGMA_RTOL
     assert np.array_equal(S, Sh)
+
+
+def test_sigma_host_buffers_through_the_abi(fci_lib):
+    """fci_sigma_host: C and sigma in host memory, pinned or pageable, with the copies
+    inside the library call; the result equals the device call bit for bit, FP64 and
+    split precision, and lands in the caller's output tensor."""
+    p = fci_problem(8, 4, 4, seed=3)
+    f = gpu_fci(p)
+    c = synth.random_vector(len(p["dets"]), seed=4)
+    for prec, sl in (("fp64", 0), ("oz_bf16", 6)):
+        d = f.sigma(torch.from_numpy(c).cuda(), precision=prec, n_slices=sl).cpu().numpy()
+        hp = f.sigma(torch.from_numpy(c).pin_memory(), precision=prec, n_slices=sl).numpy()
+        hq = f.sigma(torch.from_numpy(c.copy()), precision=prec, n_slices=sl).numpy()
+        assert np.array_equal(d, hp) and np.array_equal(d, hq)
+    out = torch.empty(len(p["dets"]), dtype=torch.float64)
+    r = f.sigma(torch.from_numpy(c), out=out)
+    assert r.data_ptr() == out.data_ptr()
+    assert np.array_equal(out.numpy(), f.sigma(torch.from_numpy(c).cuda()).cpu().numpy())
+    with pytest.raises(ValueError):
+        f.sigma(torch.from_numpy(c), out=torch.empty(3, dtype=torch.float64))
 
 
 def test_sigma_fp64_14e14o_sampled_rows(fci_lib):
