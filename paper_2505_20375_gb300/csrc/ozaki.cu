@@ -429,8 +429,11 @@ __global__ void k_to_fixed(const double *__restrict__ C, int64_t n, int s,
 // sigma_I = scale * sum over the replacements of I of sign * E_int[pq, K] + e_core C_I, in
 // int64.  Thread = beta string ib (consecutive threads, consecutive determinants), looping
 // over alpha strings; pairs are taken 8 at a time, their 16 table entries loaded first,
-// then their 16 E_int values, so that each thread keeps 16 loads in flight.  Pair-table
-// rows run to n_pair_pad (multiple of 16) and hold -1 past n_pair.
+// then their 16 E_int values (loads predicated off for absent replacements), so that each
+// thread keeps up to 16 loads in flight.  Pair-table rows run to n_pair_pad (multiple of
+// 16) and hold -1 past n_pair.  The sign is applied as x ^ -odd, and the number of odd
+// terms is added at the end ((x ^ -1) + 1 = -x; integer sums, so the bits are those of
+// the plain signed sum).
 __global__ void __launch_bounds__(256) k_scatter_int(uint32_t nsa, uint32_t nsb, int npair_pad, int log2T,
                                                      const int32_t *__restrict__ pairA,
                                                      const int32_t *__restrict__ pairB,
@@ -446,14 +449,14 @@ __global__ void __launch_bounds__(256) k_scatter_int(uint32_t nsa, uint32_t nsb,
     // E is tile-major: element (pq, K) at (K / T) * R * T + pq * T + K % T, T = 2^log2T,
     // R = ldE rows per tile (n_pair for the fused kernel, 128 for the two-pass GEMM).
     // Determinant indices are 32-bit (ndet < 2^31); a pair-table entry e is 2 x (source
-    // string) + (1 if odd) or -1, and ((x & valid) ^ odd) - odd with valid = ~(e >> 31),
-    // odd = -(e & 1) gives +x, -x or 0 (absent entries load a valid element, then drop it).
+    // string) + (1 if odd) or -1 (absent).
     const uint64_t tstride = (uint64_t)ldE << log2T;
     const uint32_t tmask = (1u << log2T) - 1u;
     for (uint32_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
         const uint32_t rowoff = ia * nsb;
         const int32_t *pa = pairA + ia, *pb = pairB + ib;
         int64_t acc = 0;
+        int32_t nodd = 0;
         for (int p0 = 0; p0 < npair_pad; p0 += 8, pa += 8 * nsa, pb += 8 * nsb) {
             int32_t ea[8], eb[8];
 #pragma unroll
@@ -464,19 +467,72 @@ __global__ void __launch_bounds__(256) k_scatter_int(uint32_t nsa, uint32_t nsb,
             int64_t xa[8], xb[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const uint32_t Ka = (uint32_t)max(ea[e] >> 1, 0) * nsb + ib;
-                const uint32_t Kb = rowoff + (uint32_t)max(eb[e] >> 1, 0);
+                const uint32_t Ka = (uint32_t)(ea[e] >> 1) * nsb + ib;
+                const uint32_t Kb = rowoff + (uint32_t)(eb[e] >> 1);
                 const uint32_t r = (uint32_t)(p0 + e) << log2T;
-                xa[e] = __ldg(E + ((uint64_t)(Ka >> log2T) * tstride + (r + (Ka & tmask))));
-                xb[e] = __ldg(E + ((uint64_t)(Kb >> log2T) * tstride + (r + (Kb & tmask))));
+                xa[e] = ea[e] >= 0 ? __ldg(E + ((uint64_t)(Ka >> log2T) * tstride + (r + (Ka & tmask)))) : 0;
+                xb[e] = eb[e] >= 0 ? __ldg(E + ((uint64_t)(Kb >> log2T) * tstride + (r + (Kb & tmask)))) : 0;
             }
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
-                const int64_t va = ~(int64_t)(ea[e] >> 31), oa = -(int64_t)(ea[e] & 1);
-                const int64_t vb = ~(int64_t)(eb[e] >> 31), ob = -(int64_t)(eb[e] & 1);
-                acc += (((xa[e] & va) ^ oa) - oa) + (((xb[e] & vb) ^ ob) - ob);
+                const int32_t oa = (ea[e] & 1) & ~(ea[e] >> 31), ob = (eb[e] & 1) & ~(eb[e] >> 31);
+                acc += (xa[e] ^ -(int64_t)oa) + (xb[e] ^ -(int64_t)ob);
+                nodd += oa + ob;
             }
         }
+        acc += nodd;
+        const uint32_t det = rowoff + ib;
+        sigma[det] = bad ? __longlong_as_double(0x7FF8000000000000ll) : scalbn(__ll2double_rn(acc), u) + e_core * C[det];
+    }
+}
+
+// The same gather-back for the two-pass layout (tiles of 64 determinants, 128 rows), with
+// compile-time tile arithmetic (IDX32: element offsets below 2^32), loads predicated off
+// for absent replacements, and the sign applied as x ^ -odd with the odd count added at
+// the end ((x ^ -1) + 1 = -x; integer sums, so the result is the same bits).
+template <bool IDX32>
+__global__ void __launch_bounds__(128) k_scatter_int2p(uint32_t nsa, uint32_t nsb, int npair_pad,
+                                                       const int32_t *__restrict__ pairA,
+                                                       const int32_t *__restrict__ pairB,
+                                                       const int64_t *__restrict__ E,
+                                                       const double *__restrict__ C, double e_core, int ushift,
+                                                       const int *__restrict__ shC, const int *__restrict__ status,
+                                                       int *__restrict__ sticky, double *__restrict__ sigma) {
+    const uint32_t ib = blockIdx.x * blockDim.x + threadIdx.x;
+    if (ib >= nsb) return;
+    const int u = ushift - *shC;
+    const bool bad = *status != 0;
+    if (bad && ib == 0 && blockIdx.y == 0) atomicExch(sticky, *status);
+    auto at = [&](uint32_t K, int row) -> const int64_t * {
+        if (IDX32) return E + (((K >> 6) << 13) + ((uint32_t)row << 6) + (K & 63u));
+        return E + ((((uint64_t)(K >> 6)) << 13) + (uint32_t)(row << 6) + (K & 63u));
+    };
+    for (uint32_t ia = blockIdx.y; ia < nsa; ia += gridDim.y) {
+        const uint32_t rowoff = ia * nsb;
+        const int32_t *pa = pairA + ia, *pb = pairB + ib;
+        int64_t acc = 0;
+        int32_t nodd = 0;
+        for (int p0 = 0; p0 < npair_pad; p0 += 8, pa += 8 * nsa, pb += 8 * nsb) {
+            int32_t ea[8], eb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                ea[e] = __ldg(pa + e * nsa);
+                eb[e] = __ldg(pb + e * nsb);
+            }
+            int64_t xa[8], xb[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                xa[e] = ea[e] >= 0 ? __ldg(at((uint32_t)(ea[e] >> 1) * nsb + ib, p0 + e)) : 0;
+                xb[e] = eb[e] >= 0 ? __ldg(at(rowoff + (uint32_t)(eb[e] >> 1), p0 + e)) : 0;
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int32_t oa = (ea[e] & 1) & ~(ea[e] >> 31), ob = (eb[e] & 1) & ~(eb[e] >> 31);
+                acc += (xa[e] ^ -(int64_t)oa) + (xb[e] ^ -(int64_t)ob);
+                nodd += oa + ob;
+            }
+        }
+        acc += nodd;
         const uint32_t det = rowoff + ib;
         sigma[det] = bad ? __longlong_as_double(0x7FF8000000000000ll) : scalbn(__ll2double_rn(acc), u) + e_core * C[det];
     }
@@ -552,9 +608,10 @@ __global__ void __launch_bounds__(64 * KCC) k_fci_split(uint32_t ndet, uint32_t 
 // coalesced runs of C_int rows.  Thread t takes pairs 8 (t / (256 / KCC)) .. + 7 of each
 // K-chunk and determinants t % (256 / KCC) + j (256 / KCC) of the row.  Used where a row
 // fits in shared memory; block 0 also writes the zero digits of the padding determinants of
-// the last tile.
+// the last tile.  Capped at 40 registers for six resident blocks per SM (the loads of the
+// pair table and of C rows are what the warps wait on; measured 11% faster at 14e/14o).
 template <int S, int KCC>
-__global__ void __launch_bounds__(256) k_fci_split_rows(uint32_t ndet, uint32_t nsa, uint32_t nsb, int npair_pad,
+__global__ void __launch_bounds__(256, 6) k_fci_split_rows(uint32_t ndet, uint32_t nsa, uint32_t nsb, int npair_pad,
                                                         int n_kc, int64_t n_nt, const int32_t *__restrict__ pairA,
                                                         const int32_t *__restrict__ pairB,
                                                         const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
@@ -962,8 +1019,13 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
     phase_scope ps(h, st, FCI_PHASE_SCATTER, 1);
     const int threads = 128;
     dim3 g((unsigned)ceil_div(h->nsb, threads), (unsigned)std::min<int64_t>(h->nsa, 65535));
-    k_scatter_int<<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair_pad, 6, h->d_pair_a, h->d_pair_b, E, OZG_M, C,
-                                       h->e_core, 8 * oz_gemm_L0(s, 8) - h->G_exp, shC, status, h->d_status, sigma);
+    const int ush = 8 * oz_gemm_L0(s, 8) - h->G_exp;
+    if ((uint64_t)n_nt * OZG_M * OZG_N < ((uint64_t)1 << 32))
+        k_scatter_int2p<true><<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair_pad, h->d_pair_a, h->d_pair_b, E, C,
+                                                     h->e_core, ush, shC, status, h->d_status, sigma);
+    else
+        k_scatter_int2p<false><<<g, threads, 0, st>>>(h->nsa, h->nsb, h->npair_pad, h->d_pair_a, h->d_pair_b, E, C,
+                                                      h->e_core, ush, shC, status, h->d_status, sigma);
     FCI_CUDA(h, cudaGetLastError());
     return FCI_OK;
 }
