@@ -982,7 +982,7 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
         // 14e/14o), else one CTA per N-tile
         const size_t row_smem = (size_t)h->nsb * 8;
         const bool rows = row_smem <= OZ_SMEM_MAX;
-        const unsigned gr = (unsigned)std::min<int64_t>(h->nsa, 152 * 6);
+        const unsigned gr = (unsigned)h->nsa;  // one block per alpha string: no tail of unequal row counts
         switch (s * 10 + tg.kcc) {
 #define OZ_SPLIT(S_, K_)                                                                                          \
     case S_ * 10 + K_:                                                                                            \
