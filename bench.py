@@ -696,7 +696,8 @@ def run_ours(a, rank, world, local_rank):
             kname = f"k_oz_contract<{n_sl},{chosen.get('dets_per_tile', 64)}>"
             kdesc = "fused producer, tcgen05.mma kind::f16"
         peak = peaks.get("bf16_tflops", 1891.0)
-        roof = split_roofline(npair, N, n_sl, ms_launch, ms_step, peak, two_pass)
+        roof = split_roofline(npair, N, n_sl, ms_launch, ms_step, peak, two_pass,
+                              tile_n=int(chosen.get("dets_per_tile") or 64))
         tr = _traffic_record(kname, a.workload)
         roof.update({"kernel": f"{kname} ({kdesc})", "traffic": tr["bytes"] if tr else None,
                      "traffic_record": tr,
