@@ -544,6 +544,10 @@ def run_ours(a, rank, world, local_rank):
                  ("oz_s7", dict(precision="oz_bf16", n_slices=7, final_precision="oz_bf16", final_slices=7)),
                  ("mixed_s3_then_oz_s7", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4,
                                               final_precision="oz_bf16", final_slices=7)),
+                 # s = 6: the fewest slices whose sigma meets the 1e-11 bar (the headline's form)
+                 ("oz_s6", dict(precision="oz_bf16", n_slices=6, final_precision="oz_bf16", final_slices=6)),
+                 ("mixed_s3_then_oz_s6", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4,
+                                              final_precision="oz_bf16", final_slices=6)),
                  ("mixed_s3_then_fp64", dict(precision="oz_bf16", n_slices=3, switch_residual=1e-4)),
                 ("oz_s7_gap_bound", dict(precision="oz_bf16", n_slices=7, final_precision="oz_bf16",
                                          final_slices=7, gap_bound=True)))

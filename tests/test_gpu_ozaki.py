@@ -151,7 +151,7 @@ def test_status_word_survives_workspace_reallocation(fci_lib, monkeypatch):
     assert e.value.code == fci.FCI_ERR_TIMEOUT
 
 
-@pytest.mark.parametrize("final", [("fp64", 0), ("oz_bf16", 7)])
+@pytest.mark.parametrize("final", [("fp64", 0), ("oz_bf16", 7), ("oz_bf16", 6)])
 def test_mixed_precision_davidson_reaches_fp64_energy(fci_lib, final):
     """3-slice sigma until ||r|| <= 1e-4, then the residual correction with an FP64-class
     sigma: the energy matches dense diagonalisation within 1e-8 Eh."""
@@ -167,11 +167,12 @@ def test_mixed_precision_davidson_reaches_fp64_energy(fci_lib, final):
     assert abs(r.energy - np.linalg.eigvalsh(H)[0]) < ENERGY_TOL
 
 
-def test_oz_davidson_fp64_class_throughout(fci_lib):
+@pytest.mark.parametrize("sl", [6, 7])
+def test_oz_davidson_fp64_class_throughout(fci_lib, sl):
     p = fci_problem(9, 4, 4, n_chol=12, seed=77, e_core=1.5)
     f = gpu_fci(p)
-    r = f.davidson(tol_residual=1e-6, tol_energy=1e-10, precision="oz_bf16", n_slices=7, switch_residual=1e-30,
-                   final_precision="oz_bf16", final_slices=7, max_iter=60)
+    r = f.davidson(tol_residual=1e-6, tol_energy=1e-10, precision="oz_bf16", n_slices=sl, switch_residual=1e-30,
+                   final_precision="oz_bf16", final_slices=sl, max_iter=60)
     r64 = f.davidson(tol_residual=1e-6, tol_energy=1e-10)
     assert r.converged and r64.converged
     assert abs(r.energy - r64.energy) < ENERGY_TOL
