@@ -11,7 +11,10 @@
 //   1. every nonzero C_K emits its single replacements J = E_sr K (alpha and beta moves
 //      from the string tables), which are the only intermediate determinants whose
 //      D[rs, J] = sum_K <J|E_rs|K> C_K can be nonzero; a hash table gives each distinct J a
-//      column, and D[rs, column] collects the (at most two: one alpha, one beta) terms;
+//      column.  D[rs, J] is then gathered per column as Algorithm 1 does: the source K of
+//      each move of J (one alpha, one beta) is looked up in the ascending nonzero addresses
+//      of K's category by exponential search (galloping, then a binary search for the
+//      lower bound), and the (at most two) values found are summed;
 //   2. E = G D over those columns only (the dense FP64 contraction of the other paths);
 //   3. every column J emits its single replacements L inside the target space: the
 //      structural support of sigma, made distinct by a second hash table and sorted
@@ -83,6 +86,7 @@ struct CsArgs {
     const int64_t *c_addr;
     const double *c_val;
     int64_t nnz_c;
+    int64_t *nz_lo;                  // [n_cat + 1]: first nonzero of each target category
     unsigned long long *hj;          // intermediate determinants J
     int32_t *hj_col;
     uint64_t hj_mask;
@@ -96,9 +100,8 @@ struct CsArgs {
     double e_core;
 };
 
-// Step 1: every move of every nonzero C_K.  pass 0 inserts J; pass 1 adds sign C_K to
-// D[pair, column(J)].
-__global__ void __launch_bounds__(256) k_cs_expand(const __grid_constant__ CsArgs a, int pass) {
+// Step 1: every move of every nonzero C_K inserts its target J.
+__global__ void __launch_bounds__(256) k_cs_expand(const __grid_constant__ CsArgs a) {
     const int nm = a.nent_a + a.nent_b;
     const int64_t total = a.nnz_c * nm;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
@@ -116,15 +119,67 @@ __global__ void __launch_bounds__(256) k_cs_expand(const __grid_constant__ CsArg
             e = a.rep_b[(int64_t)B * a.nent_b + (m - a.nent_a)];
             J = das_addr(a.d, A, (int32_t)rep_target(e));
         }
-        if (J < 0) continue;
-        if (pass == 0) {
-            if (!ht_insert(a.hj, a.hj_mask, (uint64_t)J)) atomicExch(a.counts + 2, 1ull);
-        } else {
-            const int64_t col = ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J);
-            if (col < 0) continue;
-            const double c = a.c_val[i];
-            atomicAdd(a.D + (int64_t)rep_pair(e) * a.ldd + col, rep_neg(e) ? -c : c);
+        if (J >= 0 && !ht_insert(a.hj, a.hj_mask, (uint64_t)J)) atomicExch(a.counts + 2, 1ull);
+    }
+}
+
+// Index of key in the ascending a[lo, hi), or -1: steps of 1, 2, 4, ... from lo bracket
+// the key (Algorithm 1's exponentialSearch), then a binary search finds its lower bound.
+__device__ int64_t exp_search(const int64_t *__restrict__ a, int64_t lo, int64_t hi, int64_t key) {
+    if (lo >= hi) return -1;
+    int64_t b = 1;
+    while (lo + b < hi && a[lo + b] < key) b <<= 1;
+    int64_t l = lo + (b >> 1), r = min(lo + b, hi - 1);
+    while (l < r) {
+        const int64_t m = (l + r) >> 1;
+        if (a[m] < key) l = m + 1;
+        else r = m;
+    }
+    return a[l] == key ? l : -1;
+}
+
+// nz_lo[c] = first index of a nonzero coefficient at or after the start of target category c
+// (c = n_cat: the end of the target space), by binary search.
+__global__ void k_cs_cat_ranges(const __grid_constant__ CsArgs a) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= a.d.n_cat; c += gridDim.x * blockDim.x) {
+        const int64_t key = c < a.d.n_cat ? a.d.cat_off[c] : a.d.n_det;
+        int64_t lo = 0, hi = a.nnz_c;
+        while (lo < hi) {
+            const int64_t m = (lo + hi) >> 1;
+            if (a.c_addr[m] < key) lo = m + 1;
+            else hi = m;
         }
+        a.nz_lo[c] = lo;
+    }
+}
+
+// The value of the target determinant K in the compressed C, or 0.
+__device__ __forceinline__ bool cs_coef(const CsArgs &a, int64_t K, double &v) {
+    if (K < 0 || K >= a.d.n_det) return false;
+    const int c = das_dev::find_cat(a.d.cat_off, a.d.n_cat, K);
+    const int64_t i = exp_search(a.c_addr, a.nz_lo[c], a.nz_lo[c + 1], K);
+    if (i < 0) return false;
+    v = a.c_val[i];
+    return true;
+}
+
+// D[pair, column] for every column J and pair: the alpha source and the beta source of J
+// under the pair, each looked up among the nonzero coefficients (Algorithm 1's
+// intersection of J's excitation list with the compressed vector).
+__global__ void __launch_bounds__(256) k_cs_gather(const __grid_constant__ CsArgs a, int64_t n1) {
+    const int64_t total = n1 * a.npair;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = t / a.npair;
+        const int pp = (int)(t - j * a.npair);
+        int32_t A, B;
+        int pb;
+        das_strings(a.d, a.n_cat_int, a.j_addr[j], A, B, pb);
+        double d = 0.0, v;
+        const int32_t ea = __ldg(a.pair_a + (int64_t)pp * a.d.nsa + A);
+        if (ea >= 0 && cs_coef(a, das_addr(a.d, ea >> 1, B), v)) d += (ea & 1) ? -v : v;
+        const int32_t eb = __ldg(a.pair_b + (int64_t)pp * a.d.nsb + B);
+        if (eb >= 0 && cs_coef(a, das_addr(a.d, A, eb >> 1), v)) d += (eb & 1) ? -v : v;
+        a.D[(int64_t)pp * a.ldd + j] = d;
     }
 }
 
@@ -293,7 +348,7 @@ struct CsSizes {
     uint64_t capj, capl;
     int64_t ntiles;
     size_t bytes;
-    size_t off_hj, off_hjc, off_jaddr, off_D, off_E, off_hl, off_laddr, off_tmp, off_cnt, off_hist;
+    size_t off_hj, off_hjc, off_jaddr, off_D, off_E, off_hl, off_laddr, off_tmp, off_cnt, off_hist, off_nzlo;
 };
 
 CsSizes cs_sizes(const fci_context *h, int64_t nnz_c) {
@@ -314,6 +369,7 @@ CsSizes cs_sizes(const fci_context *h, int64_t nnz_c) {
     z.off_laddr = o; o += al((size_t)z.n2max * 8);
     z.off_tmp = o; o += al((size_t)z.n2max * 8);
     z.off_hist = o; o += al((size_t)256 * z.ntiles * 8);
+    z.off_nzlo = o; o += al((size_t)(h->das.n_cat + 1) * 8);
     z.off_cnt = o; o += 256;
     z.bytes = o;
     return z;
@@ -367,6 +423,7 @@ int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_va
     a.c_addr = c_addr;
     a.c_val = c_val;
     a.nnz_c = nnz_c;
+    a.nz_lo = (int64_t *)(w + z.off_nzlo);
     a.hj = (unsigned long long *)(w + z.off_hj);
     a.hj_col = (int32_t *)(w + z.off_hjc);
     a.hj_mask = z.capj - 1;
@@ -386,13 +443,13 @@ int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_va
         FCI_CUDA(h, cudaMemsetAsync(a.hj, 0xFF, z.capj * 8, s));
         FCI_CUDA(h, cudaMemsetAsync(a.counts, 0, 256, s));
         const int64_t moves = nnz_c * (a.nent_a + a.nent_b);
-        k_cs_expand<<<grid_of(moves), 256, 0, s>>>(a, 0);
+        k_cs_expand<<<grid_of(moves), 256, 0, s>>>(a);
+        k_cs_cat_ranges<<<(unsigned)ceil_div(h->das.n_cat + 1, 256), 256, 0, s>>>(a);
         k_cs_compact<<<grid_of((int64_t)z.capj), 256, 0, s>>>(a.hj, a.hj_col, z.capj, a.j_addr, a.counts);
         FCI_CUDA(h, cudaMemcpyAsync(cnt, a.counts, sizeof cnt, cudaMemcpyDeviceToHost, s));
         FCI_CUDA(h, cudaStreamSynchronize(s));
         if (cnt[2]) return fci_fail(h, FCI_ERR_CUDA, "compressed sigma: hash table overflow");
-        FCI_CUDA(h, cudaMemsetAsync(a.D, 0, (size_t)h->npair * z.n1max * 8, s));
-        k_cs_expand<<<grid_of(moves), 256, 0, s>>>(a, 1);
+        k_cs_gather<<<grid_of((int64_t)cnt[0] * h->npair), 256, 0, s>>>(a, (int64_t)cnt[0]);
         FCI_CUDA(h, cudaGetLastError());
     }
     const int64_t n1 = (int64_t)cnt[0];

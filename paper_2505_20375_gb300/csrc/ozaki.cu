@@ -539,77 +539,21 @@ __global__ void __launch_bounds__(128) k_scatter_int2p(uint32_t nsa, uint32_t ns
 }
 
 // Two-pass path, first pass: the digit image of D for the bulk-copy GEMM.  Block (N-tile
-// nt, K-chunk kc) holds S planes of 64 determinants x 8 KCC pairs in canonical K-major
-// core matrices; one CTA of 64 KCC threads fills every K-chunk of one N-tile, thread t
-// covering determinant t % 64 (decoded once) and pairs 8 (t / 64) .. 8 (t / 64) + 7 of each
-// chunk (pair-table rows past n_pair_pad and determinants past the end give zero digits).
-// Index arithmetic is 32-bit (the caller guarantees ndet < 2^31), and the sign is
-// branch-free: an entry e of a pair table is 2 x (source string) + (1 if the excitation is
-// odd), or -1 for none; ((x & valid) ^ odd) - odd with valid = ~(e >> 31) and
-// odd = -(e & 1) gives +x, -x or 0 (the load index of an absent entry is clamped to a
-// valid element).
-template <int S, int KCC>
-__global__ void __launch_bounds__(64 * KCC) k_fci_split(uint32_t ndet, uint32_t nsa, uint32_t nsb, int npair_pad,
-                                                        int n_kc, int64_t n_nt, const int32_t *__restrict__ pairA,
-                                                        const int32_t *__restrict__ pairB,
-                                                        const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
-    constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
-    constexpr int B_PLANE = OZG_N * KCC * 16;
-    const int row = threadIdx.x & 63, cc = threadIdx.x >> 6;
-    for (int64_t nt = blockIdx.x; nt < n_nt; nt += gridDim.x) {
-        // this thread's determinant, decoded once for every K-chunk of the tile
-        const uint32_t det = (uint32_t)(nt * OZG_N + row);
-        const bool live = det < ndet;
-        const uint32_t ka = live ? det / nsb : 0u, kb = live ? det - ka * nsb : 0u;
-        const uint32_t rowoff = ka * nsb;
-        const int32_t *pa = pairA + ((uint32_t)(cc * 8) * nsa + ka);
-        const int32_t *pb = pairB + ((uint32_t)(cc * 8) * nsb + kb);
-        const uint32_t stepa = 8u * KCC * nsa, stepb = 8u * KCC * nsb;
-        uint8_t *tile = Dimg + (size_t)nt * n_kc * S * B_PLANE + ((row >> 3) * KCC + cc) * 128 + (row & 7) * 16;
-#pragma unroll 1
-        for (int kc = 0; kc < n_kc; ++kc, pa += stepa, pb += stepb) {
-            const int rs0 = kc * 8 * KCC + cc * 8;
-            int32_t ea[8], eb[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const bool ok = live && rs0 + e < npair_pad;
-                ea[e] = ok ? __ldg(pa + e * nsa) : -1;
-                eb[e] = ok ? __ldg(pb + e * nsb) : -1;
-            }
-            uint32_t ylo[8], yhi[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int64_t xa = __ldg(Cint + ((uint32_t)max(ea[e] >> 1, 0) * nsb + kb));
-                const int64_t xb = __ldg(Cint + (rowoff + (uint32_t)max(eb[e] >> 1, 0)));
-                const int64_t va = ~(int64_t)(ea[e] >> 31), oa = -(int64_t)(ea[e] & 1);
-                const int64_t vb = ~(int64_t)(eb[e] >> 31), ob = -(int64_t)(eb[e] & 1);
-                const int64_t v = (((xa & va) ^ oa) - oa) + (((xb & vb) ^ ob) - ob);
-                const uint64_t y = (uint64_t)v + bias;
-                ylo[e] = (uint32_t)y;
-                yhi[e] = (uint32_t)(y >> 32);
-            }
-            uint8_t *base = tile + (size_t)kc * S * B_PLANE;
-#pragma unroll
-            for (int j = 0; j < S; ++j) {
-                const uint32_t bj = (uint32_t)(j & 3), sel = bj | ((4u + bj) << 8);
-                uint32_t w[4];
-#pragma unroll
-                for (int e = 0; e < 8; e += 2)
-                    w[e / 2] = j < 4 ? digits_f16x2(ylo[e], ylo[e + 1], sel) : digits_f16x2(yhi[e], yhi[e + 1], sel);
-                __stcs((uint4 *)(base + j * B_PLANE), make_uint4(w[0], w[1], w[2], w[3]));  // streaming: keep C_int in L2
-            }
-        }
-    }
-}
-
-// The same digit image, one alpha string (one row of C) at a time: a block stages the C_int
-// row of its alpha string in shared memory, so the beta moves of every determinant of the
-// row read shared memory instead of scattered global words, and the alpha moves read
-// coalesced runs of C_int rows.  Thread t takes pairs 8 (t / (256 / KCC)) .. + 7 of each
-// K-chunk and determinants t % (256 / KCC) + j (256 / KCC) of the row.  Used where a row
-// fits in shared memory; block 0 also writes the zero digits of the padding determinants of
-// the last tile.  Capped at 40 registers for six resident blocks per SM (the loads of the
-// pair table and of C rows are what the warps wait on; measured 11% faster at 14e/14o).
+// nt, K-chunk kc) of the image holds S planes of 64 determinants x 8 KCC pairs in canonical
+// K-major core matrices.  One alpha string (one row of C) at a time: a block stages the
+// C_int row of its alpha string in shared memory, so the beta moves of every determinant of
+// the row read shared memory instead of scattered global words, and the alpha moves read
+// coalesced runs of C_int rows (a row is at most C(15,7) x 8 bytes = 51 KB for the at most
+// 15 orbitals of this path).  Thread t takes pairs 8 (t / (256 / KCC)) .. + 7 of each
+// K-chunk and determinants t % (256 / KCC) + j (256 / KCC) of the row; block 0 also writes
+// the zero digits of the padding determinants of the last tile (pair-table rows past
+// n_pair_pad give zero digits too).  Index arithmetic is 32-bit (the caller guarantees
+// ndet < 2^31), and the sign is branch-free: an entry e of a pair table is
+// 2 x (source string) + (1 if the excitation is odd), or -1 for none;
+// ((x & valid) ^ odd) - odd with valid = ~(e >> 31) and odd = -(e & 1) gives +x, -x or 0
+// (the load index of an absent entry is clamped to a valid element).  Capped at 40
+// registers for six resident blocks per SM (the loads of the pair table and of C rows are
+// what the warps wait on; measured 11% faster at 14e/14o).
 template <int S, int KCC>
 __global__ void __launch_bounds__(256, 6) k_fci_split_rows(uint32_t ndet, uint32_t nsa, uint32_t nsb, int npair_pad,
                                                         int n_kc, int64_t n_nt, const int32_t *__restrict__ pairA,
@@ -948,7 +892,7 @@ static int oz_num_sms(fci_context *h, int *nsm) {
     return FCI_OK;
 }
 
-// Two-pass split sigma: fixed point, D digit image (k_fci_split), bulk-copy GEMM (8-bit
+// Two-pass split sigma: fixed point, D digit image (k_fci_split_rows), bulk-copy GEMM (8-bit
 // digits, one M-tile of 128 pair rows), integer scatter.
 static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int s, void *ws, cudaStream_t st) {
     if (h->ndet >= ((int64_t)1 << 31)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision: 2^31 determinants or more");
@@ -977,26 +921,17 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
         const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(N, 256), 152 * 8);
         k_absmax_bits<<<nb, 256, 0, st>>>(C, N, maxbits);
         k_to_fixed<<<nb, 256, 0, st>>>(C, N, s, maxbits, Cint, shC);
-        const unsigned gb = (unsigned)std::min<int64_t>(n_nt, 152 * 16);
-        // row-staged image where a C row fits in shared memory (measured 3-11% faster at
-        // 14e/14o), else one CTA per N-tile
-        const size_t row_smem = (size_t)h->nsb * 8;
-        const bool rows = row_smem <= OZ_SMEM_MAX;
+        const size_t row_smem = (size_t)h->nsb * 8;  // one C row (at most 51 KB at 15 orbitals)
+        if (row_smem > OZ_SMEM_MAX) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision: %lld beta strings", (long long)h->nsb);
         const unsigned gr = (unsigned)h->nsa;  // one block per alpha string: no tail of unequal row counts
         switch (s * 10 + tg.kcc) {
 #define OZ_SPLIT(S_, K_)                                                                                          \
     case S_ * 10 + K_:                                                                                            \
-        if (rows) {                                                                                               \
-            FCI_CUDA(h, cudaFuncSetAttribute(k_fci_split_rows<S_, K_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)row_smem));                                                     \
-            k_fci_split_rows<S_, K_><<<gr, 256, row_smem, st>>>((uint32_t)N, (uint32_t)h->nsa, (uint32_t)h->nsb,   \
-                                                                h->npair_pad, n_kc, n_nt, h->d_pair_a,           \
-                                                                h->d_pair_b, Cint, Dimg);                         \
-        } else {                                                                                                  \
-            k_fci_split<S_, K_><<<gb, 64 * K_, 0, st>>>((uint32_t)N, (uint32_t)h->nsa, (uint32_t)h->nsb,            \
-                                                       h->npair_pad, n_kc, n_nt, h->d_pair_a, h->d_pair_b, Cint,  \
-                                                       Dimg);                                                     \
-        }                                                                                                         \
+        FCI_CUDA(h, cudaFuncSetAttribute(k_fci_split_rows<S_, K_>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                         (int)row_smem));                                                         \
+        k_fci_split_rows<S_, K_><<<gr, 256, row_smem, st>>>((uint32_t)N, (uint32_t)h->nsa, (uint32_t)h->nsb,       \
+                                                            h->npair_pad, n_kc, n_nt, h->d_pair_a, h->d_pair_b,   \
+                                                            Cint, Dimg);                                          \
         break;
             OZ_SPLIT(2, 2) OZ_SPLIT(3, 2) OZ_SPLIT(4, 2) OZ_SPLIT(5, 2) OZ_SPLIT(6, 2) OZ_SPLIT(7, 2)
             OZ_SPLIT(2, 4) OZ_SPLIT(3, 4) OZ_SPLIT(4, 4) OZ_SPLIT(5, 4) OZ_SPLIT(6, 4) OZ_SPLIT(7, 4)
