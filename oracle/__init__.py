@@ -16,7 +16,10 @@ What it computes, and where the paper defines it:
   * the Davidson iteration and its preconditioners ("Results", Eq. davidsonPreconditioner
     and Eq. sparsePreconditioner) in ``oracle.davidson``;
   * STP-DAS categories (occupation patterns per distributed active space) in
-    ``oracle.das``.
+    ``oracle.das``;
+  * Algorithm 1's sigma on a categorically compressed vector (per-category nonzero values
+    and local addresses, exponential search, a table keyed by target address) in
+    ``oracle.alg1``.
 
 Every function here is pinned by the ``-m "not gpu"`` tests in tests/test_oracle_*.py
 against closed forms, brute force and invariants that the paper states.

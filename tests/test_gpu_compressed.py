@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import oracle
+from oracle import alg1
 from oracle import das as odas
 from paper_2505_20375_gb300 import fci, synth
 
@@ -58,6 +59,24 @@ def test_compressed_sigma_equals_dense_sigma_on_its_support(fci_lib, spaces, ref
     dets, _ = odas.das_dets(spaces, ref, ref, nel, nel, T)
     hso, gso = oracle.spin_orbital_integrals(h, g)
     assert rel_inf(dense, oracle.sigma(hso, gso, dets, c, e_core=0.4)) <= SIGMA_RTOL
+
+
+@pytest.mark.parametrize("spaces,ref,nel,T,frac", [([3, 3, 2], [1, 2, 1], 4, 1, 0.02), ([2, 3, 3], [1, 1, 2], 4, 2, 0.01)])
+def test_compressed_sigma_against_the_oracles_algorithm_1(fci_lib, spaces, ref, nel, T, frac):
+    """The oracle's Algorithm 1 (compressed C as per-category V/A arrays, exponential
+    search, a table keyed by target address) gives the same support, address for address,
+    and the same values to the FP64 tolerance."""
+    h, g, f = das_gpu(spaces, ref, nel, T, e_core=0.4)
+    c = synth.random_vector(f.n_det, seed=5)
+    c[synth.Stream(5, tag=3).uniform(f.n_det) >= frac] = 0.0
+    nz = np.flatnonzero(c)
+    addr, val = f.sigma_compressed(torch.from_numpy(nz), torch.from_numpy(c[nz]))
+    addr, val = addr.cpu().numpy(), val.cpu().numpy()
+    ref_s = alg1.sigma_alg1(h, g, 0.4, spaces, ref, ref, nel, nel, T, alg1.compress(c, spaces, ref, ref, nel, nel, T))
+    ref_addr = np.array(sorted(ref_s))
+    assert np.array_equal(addr, ref_addr)
+    ref_val = np.array([ref_s[a] for a in ref_addr])
+    assert rel_inf(val, ref_val) <= SIGMA_RTOL
 
 
 def test_compressed_sigma_edge_cases(fci_lib):
