@@ -15,7 +15,8 @@
 //      each move of J (one alpha, one beta) is looked up in the ascending nonzero addresses
 //      of K's category by exponential search (galloping, then a binary search for the
 //      lower bound), and the (at most two) values found are summed;
-//   2. E = G D over those columns only (the dense FP64 contraction of the other paths);
+//   2. E = G D over those columns only, as the dense FP64 contraction computes it but
+//      skipping the zero entries of D (the same multiply-adds in the same order);
 //   3. every column J emits its single replacements L inside the target space: the
 //      structural support of sigma, made distinct by a second hash table and sorted
 //      (radix sort on the address), which is the compressed output order;
@@ -24,9 +25,11 @@
 //      in the first table (absent J have E = 0): the arithmetic and its order are those of
 //      the dense FP64 DAS path, so the result equals the dense sigma on the support and
 //      the dense sigma is zero elsewhere.
-// Hash tables use open addressing with linear probing over a power-of-two capacity of at
-// least twice the largest number of keys, so no probe sequence runs past a free slot; every
-// probe loop is bounded by the capacity all the same and reports an overflow instead.
+// The pair tables are read string-major (one string's row contiguous; copies built on the
+// first call and kept by the handle).  Hash tables use open addressing with linear
+// probing over a power-of-two capacity of at least twice the largest number of keys, so no
+// probe sequence runs past a free slot; every probe loop is bounded by the capacity all
+// the same and reports an overflow instead.
 #include <stdint.h>
 #include <string.h>
 
@@ -43,20 +46,20 @@ using das_dev::DasDev;
 using das_dev::make_dev;
 
 constexpr unsigned long long HT_EMPTY = ~0ull;
-constexpr int RS_THREADS = 256, RS_ITEMS = 8, RS_TILE = RS_THREADS * RS_ITEMS;  // radix sort tile
+constexpr int RS_THREADS = 256, RS_ITEMS = 32, RS_TILE = RS_THREADS * RS_ITEMS;  // radix sort tile (8192 keys)
 
 inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
-__device__ __forceinline__ uint64_t hmix(uint64_t z) {  // splitmix64 finaliser (published constants)
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
+// Home slot of key k in a table of mask + 1 (a power of two) slots: Fibonacci hashing, the
+// top log2(capacity) bits of k times 2^64 / golden ratio (one multiply and a shift).
+__device__ __forceinline__ uint64_t hslot(uint64_t k, uint64_t mask) {
+    return (k * 0x9E3779B97F4A7C15ull) >> (64 - __popcll(mask));
 }
 
 // Insert key k (>= 0) once.  Returns false if every slot was probed (cannot happen at
 // the capacities used; reported as an overflow).
 __device__ bool ht_insert(unsigned long long *keys, uint64_t mask, uint64_t k) {
-    uint64_t p = hmix(k) & mask;
+    uint64_t p = hslot(k, mask);
     for (uint64_t probe = 0; probe <= mask; ++probe) {
         const unsigned long long old = atomicCAS(keys + p, HT_EMPTY, (unsigned long long)k);
         if (old == HT_EMPTY || old == k) return true;
@@ -68,7 +71,7 @@ __device__ bool ht_insert(unsigned long long *keys, uint64_t mask, uint64_t k) {
 // Column of key k, or -1 if k is not in the table.
 __device__ int64_t ht_find(const unsigned long long *__restrict__ keys, const int32_t *__restrict__ cols, uint64_t mask,
                            uint64_t k) {
-    uint64_t p = hmix(k) & mask;
+    uint64_t p = hslot(k, mask);
     for (uint64_t probe = 0; probe <= mask; ++probe) {
         const unsigned long long v = keys[p];
         if (v == k) return cols[p];
@@ -82,7 +85,8 @@ struct CsArgs {
     DasDev d;
     int n_cat_int, nent_a, nent_b, npair;
     const uint64_t *rep_a, *rep_b;   // packed replacement lists [n_str][n_ent]
-    const int32_t *pair_a, *pair_b;  // dense pair tables [n_pair_pad][n_str]: (T << 1) | sign, or -1
+    const int32_t *pair_a, *pair_b;  // string-major pair tables [n_str][ldp]: (T << 1) | sign, or -1
+    int ldp;                         // n_pair_pad
     const int64_t *c_addr;
     const double *c_val;
     int64_t nnz_c;
@@ -175,11 +179,66 @@ __global__ void __launch_bounds__(256) k_cs_gather(const __grid_constant__ CsArg
         int pb;
         das_strings(a.d, a.n_cat_int, a.j_addr[j], A, B, pb);
         double d = 0.0, v;
-        const int32_t ea = __ldg(a.pair_a + (int64_t)pp * a.d.nsa + A);
+        const int32_t ea = __ldg(a.pair_a + (int64_t)A * a.ldp + pp);
         if (ea >= 0 && cs_coef(a, das_addr(a.d, ea >> 1, B), v)) d += (ea & 1) ? -v : v;
-        const int32_t eb = __ldg(a.pair_b + (int64_t)pp * a.d.nsb + B);
+        const int32_t eb = __ldg(a.pair_b + (int64_t)B * a.ldp + pp);
         if (eb >= 0 && cs_coef(a, das_addr(a.d, A, eb >> 1), v)) d += (eb & 1) ? -v : v;
         a.D[(int64_t)pp * a.ldd + j] = d;
+    }
+}
+
+// Step 2: E[:, J] = G D[:, J] for every column, one warp per column: the warp walks the
+// column 32 rows at a time, and for each nonzero D[rs, J] (ballot, ascending rs) every lane
+// adds G[pq, rs] D[rs, J] to its rows pq = lane + 32 i with a fused multiply-add.  These
+// are the multiply-adds of the dense product in the same order without its terms
+// G[pq, rs] x 0 (which change no bit), so E equals the dense FP64 product; the columns hold
+// only the moves into a sparse vector, so this is a small fraction of its work.
+constexpr int CS_RPL = 17;  // rows per lane: n_pair <= 544 (32 orbitals)
+__global__ void __launch_bounds__(256) k_cs_spmm(const double *__restrict__ G, int npair, const double *__restrict__ D,
+                                                 int64_t ldd, int64_t n1, double *__restrict__ E) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n1; j += nw) {
+        double acc[CS_RPL];
+#pragma unroll
+        for (int i = 0; i < CS_RPL; ++i) acc[i] = 0.0;
+        for (int r0 = 0; r0 < npair; r0 += 32) {
+            const int rs = r0 + lane;
+            const double d = rs < npair ? D[(int64_t)rs * ldd + j] : 0.0;
+            unsigned nz = __ballot_sync(0xFFFFFFFFu, d != 0.0);
+            while (nz) {
+                const int b = __ffs(nz) - 1;
+                nz &= nz - 1;
+                const double v = __shfl_sync(0xFFFFFFFFu, d, b);
+                const double *g = G + (r0 + b);
+#pragma unroll
+                for (int i = 0; i < CS_RPL; ++i) {
+                    const int pq = lane + 32 * i;
+                    if (pq < npair) acc[i] = fma(g[(int64_t)pq * npair], v, acc[i]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < CS_RPL; ++i) {
+            const int pq = lane + 32 * i;
+            if (pq < npair) E[(int64_t)pq * ldd + j] = acc[i];
+        }
+    }
+}
+
+// dst[c][r] = src[r][c] for an R x C int32 table (32 x 32 tiles through shared memory, so
+// that both the reads and the writes are coalesced).
+__global__ void k_cs_transpose(const int32_t *__restrict__ src, int64_t R, int64_t C, int32_t *__restrict__ dst) {
+    __shared__ int32_t t[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[i][threadIdx.x] = src[r * C + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int64_t c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) dst[c * R + r] = t[threadIdx.x][i];
     }
 }
 
@@ -222,24 +281,31 @@ __global__ void __launch_bounds__(256) k_cs_sigma(const __grid_constant__ CsArgs
         int pb;
         das_strings(a.d, a.d.n_cat, L, A, B, pb);
         double acc = 0.0;
-        for (int pp = 0; pp < a.npair; ++pp) {
-            const double *Ep = a.E + (int64_t)pp * a.ldd;
-            const int32_t ea = __ldg(a.pair_a + (int64_t)pp * a.d.nsa + A);
-            if (ea >= 0) {
-                const int64_t J = das_addr(a.d, ea >> 1, B);
-                const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
-                if (col >= 0) {
-                    const double e = Ep[col];
-                    acc += (ea & 1) ? -e : e;
+        const int4 *ra = reinterpret_cast<const int4 *>(a.pair_a + (int64_t)A * a.ldp);
+        const int4 *rb = reinterpret_cast<const int4 *>(a.pair_b + (int64_t)B * a.ldp);
+        for (int p4 = 0; p4 < a.npair; p4 += 4) {  // four pairs per 16-byte load of each row
+            const int4 va = __ldg(ra + p4 / 4), vb = __ldg(rb + p4 / 4);
+            const int32_t ea4[4] = {va.x, va.y, va.z, va.w}, eb4[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const double *Ep = a.E + (int64_t)(p4 + k) * a.ldd;  // rows past n_pair hold -1
+                const int32_t ea = ea4[k];
+                if (ea >= 0) {
+                    const int64_t J = das_addr(a.d, ea >> 1, B);
+                    const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
+                    if (col >= 0) {
+                        const double e = Ep[col];
+                        acc += (ea & 1) ? -e : e;
+                    }
                 }
-            }
-            const int32_t eb = __ldg(a.pair_b + (int64_t)pp * a.d.nsb + B);
-            if (eb >= 0) {
-                const int64_t J = das_addr(a.d, A, eb >> 1);
-                const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
-                if (col >= 0) {
-                    const double e = Ep[col];
-                    acc += (eb & 1) ? -e : e;
+                const int32_t eb = eb4[k];
+                if (eb >= 0) {
+                    const int64_t J = das_addr(a.d, A, eb >> 1);
+                    const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
+                    if (col >= 0) {
+                        const double e = Ep[col];
+                        acc += (eb & 1) ? -e : e;
+                    }
                 }
             }
         }
@@ -278,25 +344,48 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint64_t *__restri
     }
 }
 
-// Exclusive scan of m counts in one block of 1024 threads (each a contiguous run).
+// Exclusive scan of m counts in one block of 1024 threads, 8192 counts at a time: each
+// thread loads 8 consecutive counts (issued together) and scans them, a scan of the 1024
+// thread totals (inside each warp, then over the 32 warp totals) gives each thread its
+// offset, plus the running total of the chunks before.
 __global__ void __launch_bounds__(1024) k_rs_scan(unsigned long long *__restrict__ c, int64_t m) {
-    __shared__ unsigned long long part[1024];
-    const int64_t per = (m + 1023) / 1024, b = threadIdx.x * per, e = min(m, b + per);
-    unsigned long long s = 0;
-    for (int64_t i = b; i < e; ++i) s += c[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive Hillis-Steele scan
-        const unsigned long long v = threadIdx.x >= off ? part[threadIdx.x - off] : 0ull;
+    constexpr int IPT = 8;
+    __shared__ unsigned long long wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long carry = 0;  // the same in every thread
+    for (int64_t base = 0; base < m; base += 1024 * IPT) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * IPT;
+        unsigned long long v[IPT], tot = 0;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) v[k] = i0 + k < m ? c[i0 + k] : 0ull;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k) {
+            const unsigned long long t = v[k];
+            v[k] = tot;  // exclusive inside the thread
+            tot += t;
+        }
+        unsigned long long x = tot;  // inclusive scan of the thread totals inside the warp
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        if (warp == 0) {
+            unsigned long long t = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;  // inclusive over the warps
+        }
         __syncthreads();
-    }
-    unsigned long long run = threadIdx.x ? part[threadIdx.x - 1] : 0ull;
-    for (int64_t i = b; i < e; ++i) {
-        const unsigned long long v = c[i];
-        c[i] = run;
-        run += v;
+        const unsigned long long off = carry + (warp ? wsum[warp - 1] : 0ull) + x - tot;
+#pragma unroll
+        for (int k = 0; k < IPT; ++k)
+            if (i0 + k < m) c[i0 + k] = off + v[k];
+        carry += wsum[31];
+        __syncthreads();  // wsum is rewritten by the next chunk
     }
 }
 
@@ -398,6 +487,7 @@ int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_va
     if (!ws || ws_bytes < z.bytes || ((uintptr_t)ws & 255))
         return fci_fail(h, FCI_ERR_ARG, "workspace %zu < %zu bytes or misaligned", ws_bytes, z.bytes);
     if (z.n1max >= ((int64_t)1 << 31)) return fci_fail(h, FCI_ERR_UNSUPPORTED, "too many nonzero coefficients");
+    if (h->npair > 32 * CS_RPL) return fci_fail(h, FCI_ERR_UNSUPPORTED, "compressed sigma: %d orbital pairs", h->npair);
     FCI_CUDA(h, cudaSetDevice(h->device));
     cudaStream_t s = (cudaStream_t)stream;
     *nnz_sigma = 0;
@@ -418,8 +508,24 @@ int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_va
     a.npair = h->npair;
     a.rep_a = h->d_rep_a;
     a.rep_b = h->d_rep_b;
-    a.pair_a = h->d_pair_a;
-    a.pair_b = h->d_pair_b;
+    if (!h->d_pair_a_t) {  // string-major copies of the pair tables: one string's row is contiguous
+        const int64_t R = h->npair_pad;
+        int rc = fci_dev_alloc(h, (void **)&h->d_pair_a_t, (size_t)R * h->nsa * 4);
+        if (!rc) rc = fci_dev_alloc(h, (void **)&h->d_pair_b_t, (size_t)R * h->nsb * 4);
+        if (rc) {
+            fci_dev_free(h->d_pair_a_t);
+            h->d_pair_a_t = nullptr;
+            return rc;
+        }
+        const dim3 blk(32, 8);
+        const unsigned gy = (unsigned)ceil_div(R, 32);
+        k_cs_transpose<<<dim3((unsigned)ceil_div(h->nsa, 32), gy), blk, 0, s>>>(h->d_pair_a, R, h->nsa, h->d_pair_a_t);
+        k_cs_transpose<<<dim3((unsigned)ceil_div(h->nsb, 32), gy), blk, 0, s>>>(h->d_pair_b, R, h->nsb, h->d_pair_b_t);
+        FCI_CUDA(h, cudaGetLastError());
+    }
+    a.pair_a = h->d_pair_a_t;
+    a.pair_b = h->d_pair_b_t;
+    a.ldp = h->npair_pad;
     a.c_addr = c_addr;
     a.c_val = c_val;
     a.nnz_c = nnz_c;
@@ -456,7 +562,9 @@ int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_va
     // 2. E = G D on the n1 columns
     {
         phase_scope ps(h, s, FCI_PHASE_CONTRACT, 1);
-        FCI_CUDA(h, launch_dgemm(h->npair, n1, h->npair, h->d_G, a.D, z.n1max, a.E, z.n1max, s));
+        k_cs_spmm<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n1, 8), 152 * 16)), 256, 0, s>>>(
+            h->d_G, h->npair, a.D, z.n1max, n1, a.E);
+        FCI_CUDA(h, cudaGetLastError());
     }
     // 3. the support of sigma, distinct and sorted
     {

@@ -162,6 +162,7 @@ static void free_strings(fci_context *h) {
     fci_dev_free(h->d_str_a); fci_dev_free(h->d_str_b);
     fci_dev_free(h->d_rep_a); fci_dev_free(h->d_rep_b);
     fci_dev_free(h->d_pair_a); fci_dev_free(h->d_pair_b);
+    fci_dev_free(h->d_pair_a_t); fci_dev_free(h->d_pair_b_t);
     fci_dev_free(h->d_dstr);
     fci_dev_free(h->d_G); fci_dev_free(h->d_hd); fci_dev_free(h->d_J); fci_dev_free(h->d_K);
     fci_dev_free(h->d_Gs);
@@ -169,6 +170,7 @@ static void free_strings(fci_context *h) {
     h->d_str_a = h->d_str_b = nullptr;
     h->d_rep_a = h->d_rep_b = nullptr;
     h->d_pair_a = h->d_pair_b = nullptr;
+    h->d_pair_a_t = h->d_pair_b_t = nullptr;
     h->d_dstr = nullptr;
     h->d_G = h->d_hd = h->d_J = h->d_K = nullptr;
     h->d_Gs = nullptr;

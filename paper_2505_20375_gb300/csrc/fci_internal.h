@@ -109,6 +109,8 @@ struct fci_context {
     uint64_t *d_str_a = nullptr, *d_str_b = nullptr;
     uint64_t *d_rep_a = nullptr, *d_rep_b = nullptr;  // [ns * nent] packed entries
     int32_t *d_pair_a = nullptr, *d_pair_b = nullptr; // [npair][ns]: (target<<1)|neg or -1
+    int32_t *d_pair_a_t = nullptr, *d_pair_b_t = nullptr;  // the same, string-major [ns][npair_pad]
+                                                            // (built by the compressed sigma on first use)
 
     // contraction matrix G = 1/2 g' (packed real [npair x npair], or complex [n^2 x n^2])
     double *d_G = nullptr;
