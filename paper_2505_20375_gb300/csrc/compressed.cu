@@ -95,6 +95,7 @@ struct CsArgs {
     int32_t *hj_col;
     uint64_t hj_mask;
     int64_t *j_addr;                 // [n1]: the J of each column
+    uint32_t *bm_a, *bm_b;           // bit A (B) set: some column has alpha (beta) string A (B)
     double *D, *E;                   // [n_pair][ldd]
     int64_t ldd;
     unsigned long long *hl;          // target determinants L of the support
@@ -242,6 +243,20 @@ __global__ void k_cs_transpose(const int32_t *__restrict__ src, int64_t R, int64
     }
 }
 
+// The alpha and beta strings of every column, as bitmaps (a sigma entry looks a candidate
+// column up only if both of its strings occur in some column).
+__global__ void k_cs_mark(const __grid_constant__ CsArgs a, int64_t n1) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n1; j += (int64_t)gridDim.x * blockDim.x) {
+        int32_t A, B;
+        int pb;
+        das_strings(a.d, a.n_cat_int, a.j_addr[j], A, B, pb);
+        atomicOr(a.bm_a + (A >> 5), 1u << (A & 31));
+        atomicOr(a.bm_b + (B >> 5), 1u << (B & 31));
+    }
+}
+
+__device__ __forceinline__ bool bit(const uint32_t *__restrict__ bm, int32_t i) { return (__ldg(bm + (i >> 5)) >> (i & 31)) & 1u; }
+
 // Distinct keys of a table get consecutive columns.
 __global__ void k_cs_compact(unsigned long long *keys, int32_t *cols, uint64_t cap, int64_t *addr,
                              unsigned long long *counter) {
@@ -283,14 +298,17 @@ __global__ void __launch_bounds__(256) k_cs_sigma(const __grid_constant__ CsArgs
         double acc = 0.0;
         const int4 *ra = reinterpret_cast<const int4 *>(a.pair_a + (int64_t)A * a.ldp);
         const int4 *rb = reinterpret_cast<const int4 *>(a.pair_b + (int64_t)B * a.ldp);
-        for (int p4 = 0; p4 < a.npair; p4 += 4) {  // four pairs per 16-byte load of each row
-            const int4 va = __ldg(ra + p4 / 4), vb = __ldg(rb + p4 / 4);
+        // an alpha move keeps B and a beta move keeps A: no column has them, no lookup
+        const bool try_a = bit(a.bm_b, B), try_b = bit(a.bm_a, A);
+        const int4 none = make_int4(-1, -1, -1, -1);
+        for (int p4 = 0; p4 < a.npair && (try_a || try_b); p4 += 4) {  // four pairs per 16-byte load of a row
+            const int4 va = try_a ? __ldg(ra + p4 / 4) : none, vb = try_b ? __ldg(rb + p4 / 4) : none;
             const int32_t ea4[4] = {va.x, va.y, va.z, va.w}, eb4[4] = {vb.x, vb.y, vb.z, vb.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const double *Ep = a.E + (int64_t)(p4 + k) * a.ldd;  // rows past n_pair hold -1
                 const int32_t ea = ea4[k];
-                if (ea >= 0) {
+                if (ea >= 0 && bit(a.bm_a, ea >> 1)) {
                     const int64_t J = das_addr(a.d, ea >> 1, B);
                     const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
                     if (col >= 0) {
@@ -299,7 +317,7 @@ __global__ void __launch_bounds__(256) k_cs_sigma(const __grid_constant__ CsArgs
                     }
                 }
                 const int32_t eb = eb4[k];
-                if (eb >= 0) {
+                if (eb >= 0 && bit(a.bm_b, eb >> 1)) {
                     const int64_t J = das_addr(a.d, A, eb >> 1);
                     const int64_t col = J >= 0 ? ht_find(a.hj, a.hj_col, a.hj_mask, (uint64_t)J) : -1;
                     if (col >= 0) {
@@ -437,7 +455,8 @@ struct CsSizes {
     uint64_t capj, capl;
     int64_t ntiles;
     size_t bytes;
-    size_t off_hj, off_hjc, off_jaddr, off_D, off_E, off_hl, off_laddr, off_tmp, off_cnt, off_hist, off_nzlo;
+    size_t off_hj, off_hjc, off_jaddr, off_D, off_E, off_hl, off_laddr, off_tmp, off_cnt, off_hist, off_nzlo, off_bm;
+    size_t bm_bytes;
 };
 
 CsSizes cs_sizes(const fci_context *h, int64_t nnz_c) {
@@ -459,6 +478,8 @@ CsSizes cs_sizes(const fci_context *h, int64_t nnz_c) {
     z.off_tmp = o; o += al((size_t)z.n2max * 8);
     z.off_hist = o; o += al((size_t)256 * z.ntiles * 8);
     z.off_nzlo = o; o += al((size_t)(h->das.n_cat + 1) * 8);
+    z.bm_bytes = (size_t)((h->nsa + 31) / 32 + (h->nsb + 31) / 32) * 4;
+    z.off_bm = o; o += al(z.bm_bytes);
     z.off_cnt = o; o += 256;
     z.bytes = o;
     return z;
@@ -530,6 +551,8 @@ int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_va
     a.c_val = c_val;
     a.nnz_c = nnz_c;
     a.nz_lo = (int64_t *)(w + z.off_nzlo);
+    a.bm_a = (uint32_t *)(w + z.off_bm);
+    a.bm_b = a.bm_a + (h->nsa + 31) / 32;
     a.hj = (unsigned long long *)(w + z.off_hj);
     a.hj_col = (int32_t *)(w + z.off_hjc);
     a.hj_mask = z.capj - 1;
@@ -556,6 +579,8 @@ int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_va
         FCI_CUDA(h, cudaStreamSynchronize(s));
         if (cnt[2]) return fci_fail(h, FCI_ERR_CUDA, "compressed sigma: hash table overflow");
         k_cs_gather<<<grid_of((int64_t)cnt[0] * h->npair), 256, 0, s>>>(a, (int64_t)cnt[0]);
+        FCI_CUDA(h, cudaMemsetAsync(a.bm_a, 0, z.bm_bytes, s));
+        k_cs_mark<<<grid_of((int64_t)cnt[0]), 256, 0, s>>>(a, (int64_t)cnt[0]);
         FCI_CUDA(h, cudaGetLastError());
     }
     const int64_t n1 = (int64_t)cnt[0];
