@@ -541,10 +541,11 @@ __global__ void __launch_bounds__(128) k_scatter_int2p(uint32_t nsa, uint32_t ns
 // Two-pass path, first pass: the digit image of D for the bulk-copy GEMM.  Block (N-tile
 // nt, K-chunk kc) of the image holds S planes of 64 determinants x 8 KCC pairs in canonical
 // K-major core matrices.  One alpha string (one row of C) at a time: a block stages the
-// C_int row of its alpha string in shared memory, so the beta moves of every determinant of
-// the row read shared memory instead of scattered global words, and the alpha moves read
-// coalesced runs of C_int rows (a row is at most C(15,7) x 8 bytes = 51 KB for the at most
-// 15 orbitals of this path).  Thread t takes pairs 8 (t / (256 / KCC)) .. + 7 of each
+// C_int row of its alpha string and the row's alpha-move table entries (the same for every
+// determinant of the row) in shared memory, so the beta moves of every determinant read
+// shared memory instead of scattered global words, and the alpha moves read coalesced runs
+// of C_int rows after one shared-memory lookup (a row is at most C(15,7) x 8 bytes = 51 KB
+// for the at most 15 orbitals of this path).  Thread t takes pairs 8 (t / (256 / KCC)) .. + 7 of each
 // K-chunk and determinants t % (256 / KCC) + j (256 / KCC) of the row; block 0 also writes
 // the zero digits of the padding determinants of the last tile (pair-table rows past
 // n_pair_pad give zero digits too).  Index arithmetic is 32-bit (the caller guarantees
@@ -560,29 +561,30 @@ __global__ void __launch_bounds__(256, 6) k_fci_split_rows(uint32_t ndet, uint32
                                                         const int32_t *__restrict__ pairB,
                                                         const int64_t *__restrict__ Cint, uint8_t *__restrict__ Dimg) {
     extern __shared__ int64_t sC[];
+    int32_t *sEa = reinterpret_cast<int32_t *>(sC + nsb);  // [npair_pad]: the row's alpha-move entries
     constexpr uint64_t bias = 0x8080808080808080ull >> (8 * (8 - S));
     constexpr int B_PLANE = OZG_N * KCC * 16;
     constexpr int DPT = 256 / KCC;  // determinants of the row per pass of the block
     const int cc = threadIdx.x / DPT, dl = threadIdx.x % DPT;
-    const uint32_t stepa = 8u * KCC * nsa, stepb = 8u * KCC * nsb;
+    const uint32_t stepb = 8u * KCC * nsb;
     for (uint32_t ka = blockIdx.x; ka < nsa; ka += gridDim.x) {
         __syncthreads();  // the previous row is no longer read
         for (uint32_t i = threadIdx.x; i < nsb; i += blockDim.x) sC[i] = Cint[(size_t)ka * nsb + i];
+        for (int i = threadIdx.x; i < npair_pad; i += blockDim.x) sEa[i] = __ldg(pairA + (uint32_t)i * nsa + ka);
         __syncthreads();
         for (uint32_t kb = dl; kb < nsb; kb += DPT) {
             const uint32_t det = ka * nsb + kb;
             const int row = (int)(det & 63);
             uint8_t *tile = Dimg + (size_t)(det >> 6) * n_kc * S * B_PLANE + ((row >> 3) * KCC + cc) * 128 + (row & 7) * 16;
-            const int32_t *pa = pairA + ((uint32_t)(cc * 8) * nsa + ka);
             const int32_t *pb = pairB + ((uint32_t)(cc * 8) * nsb + kb);
 #pragma unroll 1
-            for (int kc = 0; kc < n_kc; ++kc, pa += stepa, pb += stepb) {
+            for (int kc = 0; kc < n_kc; ++kc, pb += stepb) {
                 const int rs0 = kc * 8 * KCC + cc * 8;
                 int32_t ea[8], eb[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const bool ok = rs0 + e < npair_pad;
-                    ea[e] = ok ? __ldg(pa + e * nsa) : -1;
+                    ea[e] = ok ? sEa[rs0 + e] : -1;
                     eb[e] = ok ? __ldg(pb + e * nsb) : -1;
                 }
                 uint32_t ylo[8], yhi[8];
@@ -921,7 +923,7 @@ static int oz_sigma_fci_gemm(fci_context *h, const double *C, double *sigma, int
         const unsigned nb = (unsigned)std::min<int64_t>(ceil_div(N, 256), 152 * 8);
         k_absmax_bits<<<nb, 256, 0, st>>>(C, N, maxbits);
         k_to_fixed<<<nb, 256, 0, st>>>(C, N, s, maxbits, Cint, shC);
-        const size_t row_smem = (size_t)h->nsb * 8;  // one C row (at most 51 KB at 15 orbitals)
+        const size_t row_smem = (size_t)h->nsb * 8 + (size_t)h->npair_pad * 4;  // one C row + its alpha entries
         if (row_smem > OZ_SMEM_MAX) return fci_fail(h, FCI_ERR_UNSUPPORTED, "split precision: %lld beta strings", (long long)h->nsb);
         const unsigned gr = (unsigned)h->nsa;  // one block per alpha string: no tail of unequal row counts
         switch (s * 10 + tg.kcc) {
