@@ -411,7 +411,11 @@ int fci_get_phase_times(fci_handle h, double *ms, int64_t *launches, int reset);
  *                  which returns FCI_ERR_ARG);
  *   workspace:     DEVICE, >= fci_sigma_compressed_workspace_bytes(h, nnz_c), 256-byte
  *                  aligned (bounded by nnz_c x (moves per determinant)^2 support entries).
- * Real integrals only.  FCI_ERR_ARG for addresses that are not ascending target addresses.
+ * D is gathered as Algorithm 1 does (each source looked up among its category's ascending
+ * nonzero addresses by exponential search).  On its first call the handle builds
+ * string-major copies of its pair tables (n_pair_pad x 4 bytes per alpha and per beta
+ * string) and keeps them until the strings are rebuilt.  Real integrals only, at most 32
+ * orbitals.  FCI_ERR_ARG for addresses that are not ascending target addresses.
  * Host-synchronous. */
 int fci_sigma_compressed_workspace_bytes(fci_handle h, int64_t nnz_c, size_t *bytes);
 int fci_sigma_compressed(fci_handle h, const int64_t *c_addr, const double *c_val, int64_t nnz_c,
