@@ -172,7 +172,7 @@ int fci_sigma_host_workspace_bytes(fci_handle h, int n_vec, int precision, int n
  * vector-major, same element types; must not overlap).  The call copies C into the
  * front of the DEVICE workspace on `stream`, builds sigma there as fci_sigma does, copies
  * it back into sigma_host and waits for the copy: pinned (page-locked) host buffers let
- * the copies run asynchronously at the link rate, pageable ones work through the driver's
+ * the copies run asynchronously at the link rate, pageable ones go through the CUDA driver's
  * staging.  Synchronous; it reports a device-side failure of this build as
  * fci_sync_status does (FCI_ERR_TIMEOUT, sigma_host then holds NaN) and clears it.
  *   workspace: DEVICE pointer, >= fci_sigma_host_workspace_bytes, 256-byte aligned. */

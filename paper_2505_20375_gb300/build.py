@@ -3,7 +3,7 @@
 Each .cu file under csrc/ compiles to its own object in parallel; the objects link into
 paper_2505_20375_gb300/libfci.so with the CUDA runtime linked statically, so the
 library loads on a machine without a GPU (symbols can be inspected there) and needs
-only the driver on a GPU machine.
+only the NVIDIA driver on a GPU machine.
 """
 from __future__ import annotations
 
