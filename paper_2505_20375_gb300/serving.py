@@ -306,6 +306,19 @@ class Server:
             with builder.lock:
                 for _, f, _, _ in builder.ready:
                     f.close()
+            if split or fp64:
+                # leaving on an error with solves still resident: wait for their kernels,
+                # then free each Davidson state before its handle
+                try:
+                    torch.cuda.synchronize(self.device)
+                except Exception:
+                    pass
+                for a in split + fp64:
+                    for release in (a.stepper.finish, a.f.close):
+                        try:
+                            release()
+                        except Exception:
+                            pass
         torch.cuda.synchronize()
         wall = clock() - t0
         lat = np.array([r.latency for r in results])
