@@ -4,8 +4,8 @@
 Workload: plain FCI(14e, 14o), real FP64 integrals from the seeded generator
 (28 Cholesky vectors, seed 2), N = 3432 x 3432 = 11,778,624 determinants; a step is one
 sigma build (gather of D, the contraction E = g' D, the scatter into sigma) of a unit
-random vector (seed 7) resident in HBM.  Multi-GPU runs are independent replicas
-(the path does not shard on one-GPU machines): value = sum over ranks of N * K / T.
+random vector (seed 7) resident in HBM.  Multi-GPU runs are independent replicas, one
+per GPU (the sigma build is not sharded): value = sum over ranks of N * K / T.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|oz_bf16|best]
   python bench.py --impl reference    # the CPU oracle on a bounded sample of rows
@@ -26,7 +26,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 
 
 def _peaks() -> dict:
-    """Measured peaks of this GPU pool (HBM copy GB/s, cuBLAS bf16 TF/s)."""
+    """Measured peaks of the GPU from MEASURED_PEAKS.json (HBM copy GB/s, cuBLAS bf16 TF/s),
+    else fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(path)) if os.path.exists(path) else {"bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}
 sys.path.insert(0, ROOT)
@@ -140,8 +141,13 @@ class ClockSampler:
                 break
             time.sleep(0.02)
 
+    def _discard(self):
+        self.out.close()
+        os.unlink(self.out.name)
+
     def stop(self):
         if self.proc is None:
+            self._discard()
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         try:
@@ -164,7 +170,7 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        os.unlink(self.out.name)
+        self._discard()
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),

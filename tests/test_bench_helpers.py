@@ -72,3 +72,44 @@ def test_split_roofline_counts_the_methods_packed_work():
     assert 1.29 < ex < 1.31
     assert r["step"]["tensor_floor_ms"] == pytest.approx(5.4543e12 / 1933.5e12 * 1e3, rel=1e-4)
     assert r["step"]["frac"] == pytest.approx(r["step"]["tensor_floor_ms"] / 14.65)
+
+
+def test_contraction_work_is_the_methods_dense_product():
+    """E = G D per sigma: 2 n_pair^2 N_K flop (8 per complex multiply-add), times
+    s(s+1)/2 slice products in split precision.  FCI(14e,14o) with 105 packed pairs:
+    2.60e11 flop in FP64; 24 spinors, 12 electrons (576 ordered pairs, complex): 7.18e12."""
+    fci = {"n_pair": 105, "n_det_intermediate": 11778624, "dtype": 0}
+    assert bench.contraction_work(fci, 6, fp64=True) == pytest.approx(2.597e11, rel=1e-3)
+    assert bench.contraction_work(fci, 6, fp64=False) == pytest.approx(21 * 2.597e11, rel=1e-3)
+    sp = {"n_pair": 576, "n_det_intermediate": 2704156, "dtype": 1}
+    assert bench.contraction_work(sp, 8, fp64=True) == pytest.approx(7.177e12, rel=1e-3)
+    assert bench.contraction_work(sp, 8, fp64=False) == pytest.approx(36 * 7.177e12, rel=1e-3)
+
+
+def test_clock_sampler_reads_median_clock_and_throttle_reasons(tmp_path, monkeypatch):
+    """The sampler's parse of nvidia-smi's CSV (a stand-in script prints the samples): the
+    median SM clock under load, the maximum, and every throttle reason seen Active."""
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(
+        "#!/bin/sh\n"
+        "cat <<'END'\n"
+        "0, 2070, 2070, 910.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, [N/A], 2070, 905.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1965, 2070, 1398.7, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 2070, 2070, 1120.4, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "END\n"
+        "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    s = bench.ClockSampler(0)
+    s.start()
+    rec = s.stop()
+    assert rec == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not os.path.exists(s.out.name)  # the sample file is removed
+
+    # no nvidia-smi at all: the record says so instead of inventing clocks
+    monkeypatch.setenv("PATH", str(tmp_path / "empty"))
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    assert not os.path.exists(s.out.name)
