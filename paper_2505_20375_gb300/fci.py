@@ -276,7 +276,14 @@ class FCI:
                                     p, nb, _stream(stream)))
             return dst
         Cd = C.contiguous()
-        res = torch.empty_like(Cd) if out is None else out
+        if Cd.device != self.device:
+            raise ValueError(f"C must be on the handle's device ({self.device}) or on the host")
+        if out is None:
+            res = torch.empty_like(Cd)
+        elif out.device != self.device or out.dtype != Cd.dtype or out.shape != Cd.shape or not out.is_contiguous():
+            raise ValueError("out must be a contiguous tensor of C's shape and dtype on the handle's device")
+        else:
+            res = out
         p, nb = self._workspace(self.sigma_workspace_bytes(precision, n_slices, n_vec))
         self._check(_sigma(self._h, Cd.data_ptr(), res.data_ptr(), n_vec, PRECISIONS[precision], n_slices,
                            p, nb, _stream(stream)))

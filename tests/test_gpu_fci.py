@@ -120,6 +120,12 @@ def test_sigma_host_buffers_through_the_abi(fci_lib):
     assert np.array_equal(out.numpy(), f.sigma(torch.from_numpy(c).cuda()).cpu().numpy())
     with pytest.raises(ValueError):
         f.sigma(torch.from_numpy(c), out=torch.empty(3, dtype=torch.float64))
+    # a device C takes a device output of its own shape and dtype, never a host one
+    cd = torch.from_numpy(c).cuda()
+    for bad in (torch.empty(3, dtype=torch.float64, device=cd.device), torch.empty_like(out),
+                torch.empty(2 * len(c), dtype=torch.float64, device=cd.device)[::2]):
+        with pytest.raises(ValueError):
+            f.sigma(cd, out=bad)
 
 
 def test_sigma_fp64_14e14o_sampled_rows(fci_lib):
