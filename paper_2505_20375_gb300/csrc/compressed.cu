@@ -6,8 +6,9 @@
 //
 // The paper's CPU algorithm intersects, for every intermediate determinant J, the sorted
 // excitation list of J with the sorted addresses of the nonzero coefficients (exponential
-// search), and accumulates sigma in per-category hash tables.  On the GPU the same
-// restriction to nonzero coefficients is reached from the other side, with no search:
+// search), and accumulates sigma in per-category hash tables.  On the GPU the columns J
+// are found from the other side (no scan over every J of the connected categories), D is
+// gathered with that exponential search, and sigma is gathered on its support:
 //   1. every nonzero C_K emits its single replacements J = E_sr K (alpha and beta moves
 //      from the string tables), which are the only intermediate determinants whose
 //      D[rs, J] = sum_K <J|E_rs|K> C_K can be nonzero; a hash table gives each distinct J a
