@@ -13,6 +13,8 @@
 //   N = n_pair rounded up to 16 (B operand: the G digit slices, resident in shared
 //       memory), K = the same padded n_pair.
 // s = 2 or 3 slices: s level accumulators of N columns each fit the 512 TMEM columns.
+// s = 4 .. 8 (FP64 class at 6 and 7) use the two-pass form at the end of this file: a
+// digit image of D, the shared bulk-copy GEMM with pair rows on M, and an exact int64 E.
 // At these s every |C_int| < 2^21, so C goes to int32 fixed point; the exact level
 // combination E_int (|E_int| < 2^40) is stored rounded to FP32 (24 significant bits,
 // far below the 2^-8s truncation of the split), and the scatter turns each stored value
