@@ -11,7 +11,7 @@
  * Hermitian integrals, the paper's two-spinor X2C case).  sigma is evaluated as
  *   D[rs,K] = sum_J <K|E_rs|J> C_J           (gather over single replacements)
  *   E[pq,K] = sum_rs g'_pqrs D[rs,K]          (dense contraction, on tensor cores)
- *   sigma_I = 1/2 sum_pq sum_K <I|E_pq|K> E[pq,K]   (gather-back over replacements)
+ *   sigma_I = e_core C_I + 1/2 sum_pq sum_K <I|E_pq|K> E[pq,K]   (gather-back)
  * with g'_pqrs = (pq|rs) + (h'_pq delta_rs + delta_pq h'_rs)/N_e folding the one-electron
  * term into the contraction (sum_r E_rr = N_e on an N_e-electron space).
  *
@@ -136,7 +136,9 @@ int das_build_categories(fci_handle h, int n_spaces, const int *orbs_per_space,
                          fci_stream stream);
 
 /* H_II for every determinant of the current layout into the device array diag
- * (info.n_det doubles; real also for C128, where H_II is real). */
+ * (info.n_det doubles; real also for C128, where H_II is real): the diagonal that the
+ * Davidson preconditioner divides by (Results, Eqs. davidsonPreconditioner and
+ * sparsePreconditioner).  FCI_ERR_STATE before fci_build_strings.  Asynchronous. */
 int fci_diagonal(fci_handle h, double *diag, fci_stream stream);
 
 /* ------------------------------------------------------------------- sigma */
@@ -148,8 +150,9 @@ int fci_sigma_workspace_bytes(fci_handle h, int n_vec, int precision, int n_slic
 /* sigma = H C for n_vec vectors (Methods, Eqs. sigmaL, sigmaL1e, sigmaL2e).
  *   C, sigma: DEVICE pointers, n_vec x info.n_det, vector-major, double (R64) or
  *             interleaved complex (C128); must not overlap;
- *   precision: FCI_PREC_FP64, or FCI_PREC_OZ_BF16 with n_slices 16-bit digit slices of
- *             each operand of the contraction: alpha/beta strings (R64) take 2..7
+ *   precision: FCI_PREC_FP64, or FCI_PREC_OZ_BF16 with n_slices digit slices of each
+ *             operand of the contraction (signed 8-bit digits held exactly in f16;
+ *             7-bit digits for spinor strings): alpha/beta strings (R64) take 2..7
  *             slices (n_orb <= 15; 6 and 7 reach the FP64 tolerance); the DAS layout
  *             takes 2 or 3 slices (n_orb <= 17; one fused kernel, E stored in FP32, for
  *             the first phase of a mixed-precision solve) or 4 and more while
