@@ -340,8 +340,8 @@ int fci_clear_grouped_graphs(void);
 typedef struct fci_davidson_state *fci_davidson_handle;
 
 /* Davidson driven by the caller's sigma products (same iteration as davidson_solve):
- *   davidson_begin  sets up the solve (diagonal, start vector C_guess or the unit vector
- *                   at min H_II) and requests the first product;
+ *   davidson_begin  sets up the solve (diagonal, start vector C_guess or, without one,
+ *                   the start of opts->start_mix) and requests the first product;
  *   davidson_request returns the pending request: y (DEVICE) must receive H x, with the
  *                   precision and slice count this iteration uses, and the part of the
  *                   Davidson workspace reserved for the sigma build;
