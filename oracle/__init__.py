@@ -18,7 +18,8 @@ What it computes, and where the paper defines it:
   * STP-DAS categories (occupation patterns per distributed active space) in
     ``oracle.das``;
   * Algorithm 1's sigma on a categorically compressed vector (per-category nonzero values
-    and local addresses, exponential search, a table keyed by target address) in
+    and local addresses, exponential search, a table keyed by target address), and the
+    Davidson iteration on compressed vectors (H_ii on the fly, Eq. sparsePreconditioner) in
     ``oracle.alg1``.
 
 Every function here is pinned by the ``-m "not gpu"`` tests in tests/test_oracle_*.py

@@ -121,6 +121,15 @@ MUTANTS = [
     ("alg1_beta_move_uses_alpha_string", "alg1.py",
      "v = coefficient(K, JB) if spin == 0 else coefficient(JA, K)",
      "v = coefficient(K, JB) if spin == 0 else coefficient(K, JA)"),
+    ("compressed_diagonal_without_core_energy", "alg1.py",
+     "hii[a] = float(d) + e_core",
+     "hii[a] = float(d)"),
+    ("compressed_threshold_on_the_residual_norm", "alg1.py",
+     "tv = np.where(np.abs(sv) >= eps * np.linalg.norm(sv), sv, 0.0)",
+     "tv = np.where(np.abs(sv) >= eps * np.linalg.norm(rv), sv, 0.0)"),
+    ("compressed_ritz_phase_not_aligned", "alg1.py",
+     "            if ph < 0:\n                c, sc = scale(c, -1.0), scale(sc, -1.0)",
+     "            if False:\n                c, sc = scale(c, -1.0), scale(sc, -1.0)"),
     ("alg1_constant_term_dropped", "alg1.py",
      "sigma[int(off + a)] = sigma.get(int(off + a), 0.0) + e_core * v",
      "sigma[int(off + a)] = sigma.get(int(off + a), 0.0) + 0.0 * v"),
