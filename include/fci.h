@@ -405,7 +405,9 @@ int fci_get_phase_times(fci_handle h, double *ms, int64_t *launches, int reset);
  * values, i.e. the per-category (V, A) arrays of the paper concatenated in category order
  * (a category's local address is its DAS address minus the category's offset).
  *   c_addr, c_val: DEVICE, nnz_c entries: ascending target addresses (< info.n_det) and
- *                  their coefficients (explicit zeros allowed);
+ *                  their coefficients (explicit zeros allowed: a listed zero is treated
+ *                  as a nonzero of value 0, so it widens the support below by its
+ *                  connections, where sigma is then exactly 0);
  *   out_addr, out_val: DEVICE, capacity entries: sigma on its structural support (every
  *                  target determinant that H connects to a nonzero C_K), ascending; the
  *                  values equal the FP64 sigma of the dense vector there, term by term in
