@@ -214,3 +214,20 @@ def test_builder_failure_reaches_the_caller_and_closes_handles(monkeypatch):
     assert world.max_active == 4
     assert all(h.closed for h in world.handles if h.seed != world.fail_seed)
     assert world.active == 0
+
+
+def test_solve_alone_and_capacity_use_the_same_stepper_path(monkeypatch):
+    """solve_alone runs one request through the same scheduler on its own (arrival reset to
+    0, the server's settings kept); measure_capacity solves one request of every shape in
+    both precisions and reports the mean service time."""
+    world = World()
+    world.budget = 100 * (WS_BYTES + 8 * MiB)
+    install_fakes(monkeypatch, world)
+    server = serving.Server(max_active=8, memory_budget=world.budget, split_slices=3, final_slices=6)
+    q = _requests(5)[4]
+    r = serving.solve_alone(q, server)
+    assert r.rid == q.rid and r.arrival == 0.0 and r.energy == pytest.approx(-1.0 - 1e-3 * q.seed)
+    mean, times = serving.measure_capacity(server, seed=2000)
+    assert len(times) == 2 * len(serving.MIX) and mean == pytest.approx(np.mean(list(times.values())))
+    assert world.active == 0 and all(h.closed for h in world.handles)
+    assert server.footprint(q) == WS_BYTES + 8 * MiB
