@@ -113,3 +113,26 @@ def test_clock_sampler_reads_median_clock_and_throttle_reasons(tmp_path, monkeyp
     s.start()
     assert s.stop() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
     assert not os.path.exists(s.out.name)
+
+
+def test_oracle_leg_times_sigma_rows_of_a_fixed_table():
+    """The CPU baseline: the determinant table is built once (its time reported apart), and
+    the timed sample is whole sigma rows of the oracle, never more than the space holds."""
+    import numpy as np
+
+    import oracle
+    from paper_2505_20375_gb300 import synth
+
+    w = {"n": 6, "na": 3, "nb": 3}
+    h, g = synth.real_integrals(6, 8, seed=1)
+    leg = bench.OracleLeg(w, h, g)
+    N = len(leg.dets)
+    assert N == 400 and leg.setup_s >= 0.0 and leg.threads >= 1
+    c = synth.random_vector(N, seed=7)
+    rate, rows, secs = leg.rate(c, 0.05, rng_seed=3)
+    assert 0 < rows <= N and secs > 0 and rate == pytest.approx(rows / secs)
+    # the rows it times are the oracle's sigma rows (same table, same arithmetic)
+    hso, gso = oracle.spin_orbital_integrals(h, g)
+    perm = np.random.default_rng(3).permutation(N)[:50]
+    assert np.array_equal(leg.table.sigma(leg.hso, leg.gso, c, rows=perm),
+                          oracle.sigma(hso, gso, oracle.fci_dets(6, 3, 3), c, rows=perm))
