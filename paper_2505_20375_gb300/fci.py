@@ -376,6 +376,8 @@ class FCI:
         """sigma = H C for a categorically compressed C on the DAS layout
         (fci_sigma_compressed): addr (int64, ascending DAS target addresses) and val
         (float64) on the device; returns sigma's support (ascending addresses) and values."""
+        if addr.dim() != 1 or val.shape != addr.shape:
+            raise ValueError("addr and val must be 1-D and of the same length")
         addr = addr.to(self.device, torch.int64).contiguous()
         val = val.to(self.device, torch.float64).contiguous()
         nnz = addr.numel()
